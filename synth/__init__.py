@@ -1,0 +1,198 @@
+"""Seeded synthetic inputs (graphs, edge values, dense matrices).
+
+This module serves both the CUDA library and the CPU oracle with identical
+inputs and holds none of the SpMM arithmetic.  The C source ``synth.c`` is
+compiled with gcc on first use (or by ``__graft_entry__.build()``).
+
+Graph recipes (paper Section 5 "graph datasets"; R-MAT quadrant probabilities
+a/b/c/d = 0.57/0.19/0.19/0.05):
+
+* ``rmat_csr(scale, n_edges)``: R-MAT edges, duplicates merged, self-loops kept.
+* ``chunglu_csr(g)``: graph ``g`` of a batch of Chung-Lu power-law graphs
+  (exponent 2.1, size log-uniform in [1e3, 2e5], average degree U[8, 32]).
+* ``sym_rmat_csr(scale)``: symmetrised R-MAT (8*N directed edges, union with the
+  transpose), lognormal(0,1) pair weights, normalised D^-1/2 A D^-1/2.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "synth.c")
+_LIB_PATH = os.path.join(_HERE, "libsynth.so")
+_lock = threading.Lock()
+_lib = None
+
+RMAT_ABC = (0.57, 0.19, 0.19)
+
+
+def build(force: bool = False) -> str:
+    """Compile libsynth.so in place (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            i32, i64, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+            lib.synth_philox4x32_10.argtypes = [P, P, P]
+            lib.synth_rmat_edges.argtypes = [i32, i64, f64, f64, f64, u64, P, P]
+            lib.synth_edges_to_csr.argtypes = [i64, i64, i64, P, P, i32, P, P]
+            lib.synth_edges_to_csr.restype = i64
+            lib.synth_uniform01_f32.argtypes = [u64, u64, i64, P]
+            lib.synth_dense_f32.argtypes = [u64, u64, i64, i64, i32, i64, i32, P]
+            lib.synth_dense_rows_f32.argtypes = [u64, u64, P, i64, i32, i32, P]
+            lib.synth_sample_rows.argtypes = [u64, i64, i64, P]
+            lib.synth_chunglu_size.argtypes = [u64, i64, f64, f64, f64, f64, P]
+            lib.synth_chunglu_size.restype = i64
+            lib.synth_chunglu_edges.argtypes = [u64, i64, i64, i64, f64, P, P]
+            lib.synth_chunglu_edges.restype = i32
+            lib.synth_sym_lognormal.argtypes = [u64, i64, P, P, i32, P]
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().synth_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+class CSR:
+    """A host CSR matrix: int64 row pointers, int32 column indices, optional
+    float32 values (None = pattern-only, every stored entry is 1)."""
+
+    def __init__(self, n_rows, n_cols, row_ptr, col_idx, values=None):
+        self.n_rows = int(n_rows)
+        self.n_cols = int(n_cols)
+        self.row_ptr = row_ptr
+        self.col_idx = col_idx
+        self.values = values
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.row_ptr)
+
+
+def rmat_edges(scale: int, n_edges: int, seed: int = 0, abc=RMAT_ABC):
+    src = np.empty(n_edges, dtype=np.uint32)
+    dst = np.empty(n_edges, dtype=np.uint32)
+    a, b, c = abc
+    _load().synth_rmat_edges(scale, n_edges, a, b, c, seed, _p(src), _p(dst))
+    return src, dst
+
+
+def edges_to_csr(n_rows: int, n_cols: int, src, dst, symmetrize: bool = False) -> CSR:
+    src = np.ascontiguousarray(src, dtype=np.uint32)
+    dst = np.ascontiguousarray(dst, dtype=np.uint32)
+    m = len(src) * (2 if symmetrize else 1)
+    row_ptr = np.empty(n_rows + 1, dtype=np.int64)
+    col_idx = np.empty(max(m, 1), dtype=np.int32)
+    nnz = _load().synth_edges_to_csr(n_rows, n_cols, len(src), _p(src), _p(dst), int(symmetrize),
+                                     _p(row_ptr), _p(col_idx))
+    if nnz < 0:
+        raise MemoryError("synth_edges_to_csr: allocation failed")
+    return CSR(n_rows, n_cols, row_ptr, col_idx[:nnz].copy())
+
+
+def uniform01(n: int, seed: int = 0, seed2: int = 0) -> np.ndarray:
+    out = np.empty(n, dtype=np.float32)
+    _load().synth_uniform01_f32(seed, seed2, n, _p(out))
+    return out
+
+
+def rmat_csr(scale: int, n_edges: int | None = None, seed: int = 0, weighted: bool = False,
+             abc=RMAT_ABC) -> CSR:
+    """R-MAT graph with 2^scale vertices and n_edges (default 16 * 2^scale)
+    directed edges; duplicates merged, self-loops kept.  If weighted, values are
+    U[0,1) float32 drawn per CSR position after the merge."""
+    n = 1 << scale
+    if n_edges is None:
+        n_edges = 16 * n
+    src, dst = rmat_edges(scale, n_edges, seed, abc)
+    A = edges_to_csr(n, n, src, dst)
+    del src, dst
+    if weighted:
+        A.values = uniform01(A.nnz, seed=seed, seed2=0x7661)
+    return A
+
+
+def sym_rmat_csr(scale: int, seed: int = 0, normalise: bool = True) -> CSR:
+    """Symmetrised R-MAT: 8*N directed edges, union with the transpose (a
+    self-loop is stored once), lognormal(0,1) weight per unordered pair, then
+    D^-1/2 A D^-1/2 with D the weighted degree (zero rows stay zero)."""
+    n = 1 << scale
+    src, dst = rmat_edges(scale, 8 * n, seed)
+    A = edges_to_csr(n, n, src, dst, symmetrize=True)
+    del src, dst
+    val = np.empty(A.nnz, dtype=np.float32)
+    _load().synth_sym_lognormal(seed, n, _p(A.row_ptr), _p(A.col_idx), int(normalise), _p(val))
+    A.values = val
+    return A
+
+
+def chunglu_size(g: int, seed: int = 0, nmin=1e3, nmax=2e5, dmin=8.0, dmax=32.0):
+    d = np.zeros(1, dtype=np.float64)
+    n = _load().synth_chunglu_size(seed, g, nmin, nmax, dmin, dmax, _p(d))
+    return int(n), float(d[0])
+
+
+def chunglu_csr(g: int, seed: int = 0, gamma: float = 2.1, nmin=1e3, nmax=2e5, dmin=8.0,
+                dmax=32.0, n: int | None = None, avg_deg: float | None = None) -> CSR:
+    """Graph g of a seeded batch of directed Chung-Lu power-law graphs."""
+    n0, d0 = chunglu_size(g, seed, nmin, nmax, dmin, dmax)
+    n = n0 if n is None else n
+    avg_deg = d0 if avg_deg is None else avg_deg
+    m = int(round(n * avg_deg))
+    src = np.empty(m, dtype=np.uint32)
+    dst = np.empty(m, dtype=np.uint32)
+    if _load().synth_chunglu_edges(seed, g, n, m, gamma, _p(src), _p(dst)) != 0:
+        raise MemoryError("synth_chunglu_edges: allocation failed")
+    return edges_to_csr(n, n, src, dst)
+
+
+def dense(n_rows: int, k: int, seed: int = 0, mode: str = "uniform", row0: int = 0,
+          ld: int | None = None, seed2: int = 0) -> np.ndarray:
+    """Dense float32 matrix; element (i, j) depends only on (seed, seed2, i, j).
+    mode: 'uniform' U[-1,1), 'int' integers 0..7, 'unit' U[0,1)."""
+    ld = k if ld is None else ld
+    m = {"uniform": 0, "int": 1, "unit": 2}[mode]
+    out = np.zeros((n_rows, ld), dtype=np.float32)
+    _load().synth_dense_f32(seed, seed2, row0, n_rows, k, ld, m, _p(out))
+    return out
+
+
+def dense_rows(rows, k: int, seed: int = 0, mode: str = "uniform", seed2: int = 0) -> np.ndarray:
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    m = {"uniform": 0, "int": 1, "unit": 2}[mode]
+    out = np.empty((len(rows), k), dtype=np.float32)
+    _load().synth_dense_rows_f32(seed, seed2, _p(rows), len(rows), k, m, _p(out))
+    return out
+
+
+def sample_rows(n_rows: int, n: int, seed: int = 0) -> np.ndarray:
+    out = np.empty(n, dtype=np.int64)
+    _load().synth_sample_rows(seed, n_rows, n, _p(out))
+    return out

@@ -1,0 +1,59 @@
+"""Plant plausible mistakes in a copy of oracle.c (on the CPU) and check that
+the pins fail on each one.  A pin that cannot tell a mutant from the real
+oracle would not be pinning anything."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from tests import test_oracle_apps as apps
+from tests import test_oracle_spmm as sp
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+
+MUTANTS = {
+    # forward product reads the output row's own X row (wrong index)
+    "fwd_wrong_index": ("* xget(X, xtype, (int64_t)col_idx[p] * ldx + j);\n                Y[i * ldy + j] = s;",
+                        "* xget(X, xtype, (int64_t)i * ldx + j);\n                Y[i * ldy + j] = s;",
+                        [lambda: sp.test_vs_dense_matmul(0, True, 3)]),
+    # forward product drops the edge value
+    "fwd_drop_value": ("s += vget(val, vtype, p) * xget(X, xtype, (int64_t)col_idx[p] * ldx + j);",
+                       "s += xget(X, xtype, (int64_t)col_idx[p] * ldx + j);",
+                       [lambda: sp.test_vs_dense_matmul(1, True, 1)]),
+    # transposed product uses the transposed operand's row
+    "t_transposed_operand": ("Y[c * ldy + j] += a * xget(X, xtype, i * ldx + j);",
+                             "Y[c * ldy + j] += a * xget(X, xtype, c * ldx + j);",
+                             [sp.test_cycle_shifts_rows]),
+    # PageRank forgets the dangling mass
+    "pr_no_dangling": ("d * dangling / (double)n;", "0.0 * dangling;",
+                       [apps.test_pagerank_two_node_closed_form, apps.test_pagerank_vs_dense_google_matrix]),
+    # PageRank forgets to divide by the out-degree
+    "pr_no_outdegree": ("double share = x[v] / (double)L;", "double share = x[v];",
+                        [apps.test_pagerank_vs_dense_google_matrix]),
+    # NMF objective with the cross term's factor 2 dropped
+    "nmf_objective_cross": ("return a2 - 2.0 * cross + quad;", "return a2 - cross + quad;",
+                            [lambda: apps.test_nmf_vs_dense_updates(False)]),
+    # NMF W update with an off-by-one numerator column
+    "nmf_w_numerator": ("W[i * k + r] *= AH[i * k + r] / (den[r] + eps);",
+                        "W[i * k + r] *= AH[i * k + (r + 1) % k] / (den[r] + eps);",
+                        [lambda: apps.test_nmf_vs_dense_updates(True)]),
+    # Jacobi rotation with the wrong sign on one side
+    "jacobi_sign": ("M[p * m + r] = c * mpr - s * mqr;", "M[p * m + r] = c * mpr + s * mqr;",
+                    [apps.test_jacobi_vs_numpy_eigh]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new, pins = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mpath = tmp_path / "oracle_mut.c"
+    mpath.write_text(src.replace(old, new))
+    lib = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-shared", "-fPIC", "-o", str(lib), str(mpath), "-lm"])
+    with oracle.using_library(str(lib)):
+        for pin in pins:
+            with pytest.raises(AssertionError):
+                pin()

@@ -1,0 +1,386 @@
+"""SpMM benchmark: in-HBM Y = A X on an R-MAT scale-24 power-law graph.
+
+Workload (one step): Y = A X for every k in the sweep {1, 2, 4, 8, 16, 32, 64}
+with float32 X, A the pattern-only adjacency matrix of a seeded R-MAT graph
+(2^24 vertices, 2^28 generated directed edges, a/b/c/d = .57/.19/.19/.05,
+duplicates merged).  The headline value is nonzeros processed per second over
+the whole step (sum over k of nnz / step time).  Per k the line also reports
+nnz/s, the algorithmic bytes moved per call
+    nnz*(4 + value bytes) + 8*(N+1) + N*k*(X element bytes) + N*k*4
+as GB/s and as a fraction of the measured HBM copy bandwidth, and the BF16-X
+speedup with its error against the FP64 oracle on sampled rows.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+UNIT = "nnz/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=24)
+    ap.add_argument("--edge-factor", type=int, default=16)
+    ap.add_argument("--ks", default="1,2,4,8,16,32,64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def metric_name(args):
+    return f"SpMM nonzeros/s (R-MAT scale {args.scale}, k sweep {args.ks}, FP32 X)"
+
+
+def alg_bytes(nnz, n_rows, n_cols, k, xbytes, vbytes=0):
+    return nnz * (4 + vbytes) + 8 * (n_rows + 1) + n_cols * k * xbytes + n_rows * k * 4
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_graph(args):
+    t = time.time()
+    A = synth.rmat_csr(args.scale, args.edge_factor << args.scale, seed=0)
+    return A, time.time() - t
+
+
+def cpu_sample_rows(A, target_nnz, seed=7):
+    """Seeded sample of rows whose nonzeros add up to about target_nnz."""
+    n = A.n_rows
+    avg = max(A.nnz / max(n, 1), 1e-9)
+    m = int(min(n, max(64, target_nnz / avg)))
+    rows = np.unique(synth.sample_rows(n, m, seed=seed))
+    nz = int(np.diff(A.row_ptr)[rows].sum())
+    return rows, nz
+
+
+def run_cpu_oracle(A, Xh, ks, rows, threads):
+    import oracle
+    t = time.perf_counter()
+    for k in ks:
+        oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xh, rows, threads=threads, k=k)
+    return time.perf_counter() - t
+
+
+def reference_arm(args, rank, world):
+    """The FP64 CPU oracle, timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    ks = [int(k) for k in args.ks.split(",")]
+    A, _ = make_graph(args)
+    kmax = max(ks)
+    Xh = synth.dense(A.n_cols, kmax, seed=0)
+    threads = oracle.num_threads()
+    # size the per-step sample so one step takes about cpu_seconds / 4
+    rows, nz = cpu_sample_rows(A, 2_000_000)
+    dt = run_cpu_oracle(A, Xh, ks, rows, threads)
+    rate = nz * len(ks) / dt
+    target = rate * max(args.cpu_seconds / 4, 0.5) / len(ks)
+    rows, nz = cpu_sample_rows(A, target, seed=8)
+    for _ in range(args.warmup):
+        run_cpu_oracle(A, Xh, ks, rows[: max(1, len(rows) // 8)], threads)
+    times = [run_cpu_oracle(A, Xh, ks, rows, threads) for _ in range(args.steps)]
+    total = sum(times)
+    value = nz * len(ks) * args.steps / total
+    line = {
+        "impl": "reference", "metric": metric_name(args), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"rmat{args.scale}-spmm-ksweep", "scale": args.scale, "n": A.n_rows,
+                   "nnz": A.nnz, "ks": ks},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{len(rows)} seeded rows ({nz} nonzeros) of the scale-{args.scale} graph, "
+                                   f"all k in the sweep, per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1602_02864_gb300 import spmm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ks = [int(k) for k in args.ks.split(",")]
+    A, t_gen = make_graph(args)
+    N, nnz = A.n_rows, A.nnz
+    t0 = time.time()
+    h = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None)
+    torch.cuda.synchronize()
+    t_create = time.time() - t0
+    info = h.info()
+    kmax = max(ks)
+    Xh = synth.dense(N, kmax, seed=0)
+    X64 = torch.from_numpy(Xh).to(dev)
+    X = {k: X64[:, :k].contiguous() for k in ks}
+    Y = {k: torch.empty((N, k), dtype=torch.float32, device=dev) for k in ks}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    launches_per_apply = 1 + (1 if info["n_split_rows"] > 0 else 0)
+
+    def step(xs, ev=None):
+        for i, k in enumerate(ks):
+            if ev is not None:
+                ev[i][0].record(stream)
+            h.apply(xs[k], Y=Y[k])
+            if ev is not None:
+                ev[i][1].record(stream)
+
+    # ---- warm-up, then the timed steps (L2 flushed before every step)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(X)
+    barrier()
+    per_k = {k: [] for k in ks}
+    step_ms = []
+    peak_gbs, peak_kind = load_peaks()
+    with ClockSampler(local) as clk:
+        barrier()
+        for _ in range(args.steps):
+            flush.zero_()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in ks]
+            step(X, ev)
+            torch.cuda.synchronize()
+            ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(len(ks))]
+            for i, k in enumerate(ks):
+                per_k[k].append(ms[i])
+            step_ms.append(sum(ms))
+        barrier()
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = world * nnz * len(ks) * args.steps / t_total
+
+    # ---- per-k breakdown; roofline of the dominant launch
+    breakdown = {}
+    for k in ks:
+        ms = statistics.mean(per_k[k])
+        B = alg_bytes(nnz, N, N, k, 4)
+        breakdown[str(k)] = {"ms": round(ms, 4), "nnz_per_s": nnz / (ms / 1e3), "alg_GBps": B / (ms / 1e3) / 1e9,
+                             "roofline_frac": B / (ms / 1e3) / 1e9 / peak_gbs}
+    kdom = max(ks, key=lambda k: statistics.mean(per_k[k]))
+    dom = breakdown[str(kdom)]
+
+    # ---- BF16 X: speedup over FP32 and error on sampled rows vs the oracle
+    import oracle
+    othreads = oracle.num_threads()
+    sample = np.unique(synth.sample_rows(N, 2000, seed=3))
+    sample_t = torch.from_numpy(sample).to(dev)
+    absX = np.abs(Xh)
+    scale = {k: oracle.spmm_rows(A.row_ptr, A.col_idx, None, absX, sample, threads=othreads, k=k) for k in ks}
+    del absX
+    bf16 = {}
+    if not args.no_bf16:
+        for k in ks:
+            xb = X[k].to(torch.bfloat16)
+            yb = torch.empty_like(Y[k])
+            for _ in range(3):
+                h.apply(xb, Y=yb)
+            ts = []
+            for _ in range(max(3, args.steps)):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.apply(xb, Y=yb)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.mean(ts)
+            Xr = xb.float().cpu().numpy()          # bf16 values widen exactly to float32
+            ref = oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xr, sample, threads=othreads)
+            err = np.abs(yb.index_select(0, sample_t).cpu().numpy().astype(np.float64) - ref)
+            del Xr
+            B = alg_bytes(nnz, N, N, k, 2)
+            bf16[str(k)] = {"ms": round(ms, 4), "speedup_vs_f32": breakdown[str(k)]["ms"] / ms,
+                            "nnz_per_s": nnz / (ms / 1e3), "alg_GBps": B / (ms / 1e3) / 1e9,
+                            "roofline_frac": B / (ms / 1e3) / 1e9 / peak_gbs,
+                            "max_err_over_absprod": float((err / np.maximum(scale[k], 1e-300)).max())}
+            del xb, yb
+
+    # ---- parity on sampled rows (FP32 path vs FP64 oracle)
+    parity = {}
+    for k in ks:
+        ref = oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xh, sample, threads=othreads, k=k)
+        got = Y[k].index_select(0, sample_t).cpu().numpy().astype(np.float64)
+        parity[str(k)] = float((np.abs(got - ref) / np.maximum(scale[k], 1e-300)).max())
+
+    # ---- end to end: pinned host X -> device, apply, Y -> pinned host
+    e2e = None
+    if not args.no_e2e:
+        Xp = {k: X[k].cpu().pin_memory() for k in ks}
+        Yp = {k: torch.empty((N, k), dtype=torch.float32).pin_memory() for k in ks}
+        Xd = {k: torch.empty_like(X[k]) for k in ks}
+        for _ in range(2):
+            for k in ks:
+                Xd[k].copy_(Xp[k], non_blocking=True)
+                h.apply(Xd[k], Y=Y[k])
+                Yp[k].copy_(Y[k], non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(args.steps, 5))
+        e0.record(stream)
+        for _ in range(reps):
+            for k in ks:
+                Xd[k].copy_(Xp[k], non_blocking=True)
+                h.apply(Xd[k], Y=Y[k])
+                Yp[k].copy_(Y[k], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = e0.elapsed_time(e1) / 1e3
+        hb = sum(N * k * 4 for k in ks)
+        e2e = {"value": world * nnz * len(ks) * reps / te, "unit": UNIT, "h2d_bytes_per_step": hb,
+               "d2h_bytes_per_step": hb}
+        del Xp, Yp, Xd
+
+    # ---- CPU baseline: the oracle on a bounded row sample, all host cores
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = oracle.num_threads()
+        rows, nz = cpu_sample_rows(A, 1_000_000)
+        dt = run_cpu_oracle(A, Xh, ks, rows, threads)
+        target = nz * args.cpu_seconds / max(dt, 1e-3) / 2
+        rows, nz = cpu_sample_rows(A, target, seed=9)
+        dt = run_cpu_oracle(A, Xh, ks, rows, threads)
+        cpu = {"value": nz * len(ks) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{len(rows)} seeded rows ({nz} nonzeros) of the scale-{args.scale} graph, "
+                         f"FP64, every k in the sweep ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": metric_name(args), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"rmat{args.scale}-spmm-ksweep", "scale": args.scale, "n": N, "nnz": nnz,
+                       "generated_edges": args.edge_factor << args.scale, "ks": ks, "values": "pattern",
+                       "l2": "flushed (512 MB write) before every step; inputs > L2",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "per_k": breakdown,
+            "bf16": bf16,
+            "parity_max_err_over_absprod": parity,
+            "roofline": {"bound": "hbm", "achieved": dom["alg_GBps"], "peak": peak_gbs, "unit": "GB/s",
+                         "frac": dom["roofline_frac"], "traffic": None, "kernel": f"rows_kernel k={kdom} f32",
+                         "peak_kind": peak_kind},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "gpu_launches": launches_per_apply * len(ks) * args.steps,
+            "setup_s": {"generate": round(t_gen, 2), "create": round(t_create, 2)},
+            "plan": {"tasks": info["n_tasks"], "split_rows": info["n_split_rows"], "segments": info["n_segments"]},
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

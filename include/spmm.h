@@ -1,0 +1,186 @@
+/*
+ * spmm.h -- C-ABI of the GB300 sparse-matrix x dense-matrix library.
+ *
+ * The library computes Y = A X and Y = A^T X for a sparse n_rows x n_cols
+ * matrix A (the adjacency matrix of a power-law graph, optionally weighted)
+ * and a dense, row-major X with k = 1..64 columns: the operation of the
+ * paper's Section 3 and Algorithm 1 ("SparseMatrixMultiply": every nonzero
+ * a_ij of a sparse row adds a_ij * inM[j, :] to output row i; the dense
+ * matrices are kept row-major, Section 3.3).
+ *
+ * Conventions for every entry point:
+ *   - Status: every call returns an spmm_status (0 = success, < 0 = error).
+ *     No exception or abort crosses this boundary.  On error the message is
+ *     available from spmm_last_error() (per calling thread) and any handle
+ *     passed in is left unchanged.
+ *   - Streams: work is enqueued on the given CUDA stream (cudaStream_t passed
+ *     as void*, NULL = the legacy default stream).  spmm_apply does not
+ *     synchronise the host and allocates nothing.
+ *   - Memory: X and Y are caller-owned DEVICE pointers; Y is overwritten, not
+ *     accumulated into; X and Y must not overlap.  Handles own device copies of
+ *     A made at create time.
+ *   - Index types: row pointers are int64 (nnz may exceed 2^31), column
+ *     indices are int32 (n_cols < 2^31).
+ */
+#ifndef SPMM_H
+#define SPMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spmm_mat* spmm_mat_t;   /* opaque, owned by the library */
+
+typedef enum {
+    SPMM_F32 = 0,
+    SPMM_BF16 = 1,
+    SPMM_F16 = 2,
+    SPMM_F64 = 3
+} spmm_dtype;
+
+typedef enum {
+    SPMM_OK = 0,
+    SPMM_ERR_ARG = -1,          /* a bad argument (null pointer, size, dtype, alignment) */
+    SPMM_ERR_CUDA = -2,         /* a CUDA runtime call failed                            */
+    SPMM_ERR_OOM = -3,          /* device or host allocation failed                      */
+    SPMM_ERR_FORMAT = -4,       /* the sparse matrix is malformed                        */
+    SPMM_ERR_TIMEOUT = -5,      /* a bounded device-side wait ran out                    */
+    SPMM_ERR_UNSUPPORTED = -6   /* a valid but unimplemented combination                 */
+} spmm_status;
+
+/* create flags */
+#define SPMM_WANT_TRANSPOSE 0x1u   /* also build the transposed (CSC) copy for A^T X */
+
+/* Tuning knobs of the warp-task plan (the GPU form of the paper's tile-row
+ * batches, Section 3.4); a NULL pointer or a zero field selects the default.
+ *   task_nnz   nonzeros per task of short rows; segment length of split
+ *              rows                                            default 256, 32..512
+ *   task_rows  rows per task of short rows                     default 64, 1..64
+ *   long_row   rows with more nonzeros are split into segments
+ *              combined in a fixed order (deterministic)       default 512, task_nnz..512
+ *   short_max  rows with at most this many nonzeros are "short"
+ *              (one lane group per row); longer rows get a
+ *              whole warp                                      default 31, < task_nnz
+ *   x_l2_policy  L2 cache policy of the X gathers: 0 = default
+ *              (evict-last), 1 = evict-normal, 2 = evict-last; the
+ *              streamed matrix is always read evict-first
+ */
+typedef struct {
+    int32_t task_nnz;
+    int32_t task_rows;
+    int32_t long_row;
+    int32_t short_max;
+    int32_t x_l2_policy;
+    int32_t reserved[3];
+} spmm_opts;
+
+/* Plan statistics reported by spmm_get_info. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    int64_t n_tasks;             /* warp tasks of the forward plan                  */
+    int64_t n_split_rows;        /* rows split into segments                        */
+    int64_t n_segments;          /* segment tasks (one partial result each)         */
+    int64_t n_tasks_t;           /* the same three for the transposed plan (or 0)   */
+    int64_t n_split_rows_t;
+    int64_t n_segments_t;
+    int64_t device_bytes;        /* device memory held by the handle                */
+    int32_t value_dtype;         /* spmm_dtype of the stored values, -1 = pattern   */
+    int32_t has_transpose;
+} spmm_info;
+
+/*
+ * spmm_create_csr -- build a handle from a CSR matrix in HOST memory
+ * (Section 3.2 stores the matrix once in a compact format before any
+ * multiplication; here the one-time step is validation, a copy to HBM, the
+ * warp-task plan and, with SPMM_WANT_TRANSPOSE, a CSC copy for A^T X).
+ *   out        receives the handle
+ *   n_rows, n_cols  matrix shape, 0 <= n_rows, 1 <= n_cols < 2^31
+ *   nnz        stored entries = row_ptr[n_rows]
+ *   row_ptr    n_rows+1 int64, row_ptr[0] = 0, non-decreasing
+ *   col_idx    nnz int32, 0 <= col < n_cols (any order within a row)
+ *   values     nnz values of type vtype, or NULL for a pattern matrix (all 1)
+ *   vtype      SPMM_F32, SPMM_BF16 or SPMM_F16 (ignored when values is NULL)
+ *   flags      SPMM_WANT_TRANSPOSE or 0
+ *   opts       tuning knobs or NULL
+ *   stream     stream for the copies; the call returns after they finish
+ * Errors: SPMM_ERR_ARG (null/shape), SPMM_ERR_FORMAT (row_ptr not monotone,
+ * wrong row_ptr[0] or row_ptr[n_rows], column out of range), SPMM_ERR_OOM,
+ * SPMM_ERR_CUDA.  The input arrays are copied; the caller keeps ownership.
+ */
+int spmm_create_csr(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, int64_t nnz,
+                    const int64_t* row_ptr, const int32_t* col_idx, const void* values,
+                    spmm_dtype vtype, uint32_t flags, const spmm_opts* opts, void* stream);
+
+/*
+ * spmm_apply -- Y = A X (transpose = 0) or Y = A^T X (transpose = 1)
+ * (Algorithm 1; A^T X is the W^T A / A H^T product of Section 4.3).
+ *   X      device, row-major, rows = n_cols (A X) or n_rows (A^T X), leading
+ *          dimension ldx >= k, element type xtype (F32, BF16 or F16)
+ *   k      1..64 dense columns
+ *   Y      device, row-major float32 (ytype must be SPMM_F32), rows = n_rows
+ *          (A X) or n_cols (A^T X), leading dimension ldy >= k; only the first
+ *          k columns of each row are written
+ * Accumulation is float32 in a fixed order: repeated calls give bit-identical
+ * results.  Asynchronous on `stream`; allocates nothing.
+ * Errors: SPMM_ERR_ARG (null, k out of range, ld < k, dtype, transpose without
+ * SPMM_WANT_TRANSPOSE), SPMM_ERR_CUDA (launch failure).
+ */
+int spmm_apply(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype xtype, void* Y,
+               int64_t ldy, spmm_dtype ytype, int32_t transpose, void* stream);
+
+/*
+ * spmm_sync_status -- synchronise `stream` and report whether any call on A
+ * since the last check hit a device-side timeout.  The kernels stage the
+ * matrix with asynchronous copies and wait for them with a bound (2 s); a
+ * wait that runs out marks the handle, leaves that call's output incomplete
+ * and returns SPMM_ERR_TIMEOUT here (the mark is then cleared).  Not a
+ * paper operation: the failure-detection side of the asynchronous staging.
+ */
+int spmm_sync_status(spmm_mat_t A, void* stream);
+
+/*
+ * spmm_debug_wait_timeout -- diagnostic: run a one-warp kernel whose staging
+ * wait can never complete (it announces a transfer it never issues), with a
+ * bound of wait_ns nanoseconds, and report SPMM_ERR_TIMEOUT when the bound
+ * ran out as intended (SPMM_OK would mean the timeout path is broken).
+ * Synchronises `stream`; faults nothing.
+ */
+int spmm_debug_wait_timeout(uint64_t wait_ns, void* stream);
+
+/*
+ * spmm_plan_tasks -- host-only: build the warp-task plan spmm_create_csr
+ * would build for this row-pointer array (no GPU work, no device memory).
+ *   row_ptr   n_rows+1 int64 (host)
+ *   opts      tuning knobs or NULL
+ *   tasks     NULL, or room for *n_tasks + 1 descriptors of 4 int32 each:
+ *             {r0, x, lo32(e0), hi32(e0)}; x >= 1: rows r0..r0+x-1 (short
+ *             rows), x == 0: the long row r0, x < 0: a segment of split row r0
+ *             writing partial slot -x-1; e0 = first nonzero; the last
+ *             descriptor is a sentinel whose e0 is nnz
+ *   n_tasks   in: capacity of `tasks` in descriptors (ignored if tasks is
+ *             NULL); out: number of tasks (without the sentinel)
+ *   n_split_rows, n_segments  out (may be NULL)
+ * Errors: SPMM_ERR_ARG (null row_ptr or n_tasks, capacity too small),
+ * SPMM_ERR_FORMAT (row_ptr not monotone or row_ptr[0] != 0).
+ */
+int spmm_plan_tasks(int64_t n_rows, const int64_t* row_ptr, const spmm_opts* opts, int32_t* tasks,
+                    int64_t* n_tasks, int64_t* n_split_rows, int64_t* n_segments);
+
+/* spmm_get_info -- plan statistics of a handle (host call, no GPU work). */
+int spmm_get_info(spmm_mat_t A, spmm_info* info);
+
+/* spmm_destroy -- free a handle and its device memory (synchronises the
+ * device work that uses it).  NULL is accepted and ignored. */
+int spmm_destroy(spmm_mat_t A);
+
+/* spmm_last_error -- message of the last failing call on this thread
+ * ("" if none).  The pointer stays valid until the thread's next call. */
+const char* spmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMM_H */

@@ -134,13 +134,17 @@ def spmm(n_rows, n_cols, row_ptr, col_idx, values, X, transpose=False, threads=1
     return Y
 
 
-def spmm_rows(row_ptr, col_idx, values, X, rows, threads=1) -> np.ndarray:
-    """Forward product for the listed output rows: returns len(rows) x k."""
+def spmm_rows(row_ptr, col_idx, values, X, rows, threads=1, k=None) -> np.ndarray:
+    """Forward product for the listed output rows: returns len(rows) x k.
+    With k given, only the first k columns of the (contiguous) X are used,
+    without copying it."""
     rp, ci = _csr(row_ptr, col_idx)
     v, vt = _vals(values)
     Xc, xt = _dense(X)
     rows = np.ascontiguousarray(rows, dtype=np.int64)
-    k = Xc.shape[1]
+    k = Xc.shape[1] if k is None else int(k)
+    if not 1 <= k <= Xc.shape[1]:
+        raise ValueError("k out of range")
     Y = np.zeros((len(rows), k), dtype=np.float64)
     _load().oracle_spmm_rows(_p(rp), _p(ci), _p(v), vt, _p(Xc), xt, Xc.shape[1], k, _p(rows), len(rows),
                              _p(Y), int(threads))

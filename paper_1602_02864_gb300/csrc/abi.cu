@@ -1,0 +1,369 @@
+// abi.cu -- the extern "C" entry points declared in include/spmm.h.
+//
+// spmm_create_csr validates the CSR input on the host, builds the warp-task
+// plan (plan.cpp), copies the matrix and the plan to HBM, and optionally
+// builds the transposed copy (a stable counting sort by column, so the
+// transposed rows list their entries in increasing original-row order).
+// spmm_apply only launches kernels: it allocates nothing and never
+// synchronises the host.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace spmm {
+
+static thread_local std::string g_error;
+constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every device-side staging wait (2 s)
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+static int cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SPMM_ERR_OOM : SPMM_ERR_CUDA;
+}
+
+static size_t dtype_size(int32_t t) {
+    switch (t) {
+        case SPMM_F32: return 4;
+        case SPMM_BF16: return 2;
+        case SPMM_F16: return 2;
+        case SPMM_F64: return 8;
+        default: return 0;
+    }
+}
+
+static void free_dev(DevCSR& d) {
+    cudaFree(d.row_ptr);
+    cudaFree(d.col_idx);
+    cudaFree(d.val);
+    cudaFree(d.tasks);
+    cudaFree(d.splits);
+    cudaFree(d.partials);
+    d = DevCSR{};
+}
+
+// Copy count elements to a new device array with `pad` zeroed elements after
+// them (the task kernel widens its bulk copies to 16-byte boundaries).
+template <typename T>
+static cudaError_t upload(T** dst, const T* src, size_t count, size_t pad, cudaStream_t s, int64_t* bytes) {
+    *dst = nullptr;
+    if (count + pad == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)dst, (count + pad) * sizeof(T));
+    if (e != cudaSuccess) { *dst = nullptr; return e; }
+    *bytes += (int64_t)((count + pad) * sizeof(T));
+    if (pad && (e = cudaMemsetAsync(*dst + count, 0, pad * sizeof(T), s)) != cudaSuccess) return e;
+    if (count == 0) return cudaSuccess;
+    return cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+// Copy one orientation (host CSR) and its plan to the device.
+static int build_orientation(DevCSR& d, int64_t n_rows, int64_t n_cols, const int64_t* row_ptr,
+                             const int32_t* col_idx, const void* val, size_t vsize, const Params& p,
+                             cudaStream_t s, int64_t* bytes) {
+    d.n_rows = n_rows;
+    d.n_cols = n_cols;
+    d.nnz = row_ptr[n_rows];
+    HostPlan plan = build_plan(row_ptr, n_rows, p);
+    cudaError_t e;
+    if ((e = upload(&d.row_ptr, row_ptr, (size_t)n_rows + 1, 2, s, bytes)) != cudaSuccess)
+        return cuda_fail(e, "row_ptr");
+    if ((e = upload(&d.col_idx, col_idx, (size_t)d.nnz, 8, s, bytes)) != cudaSuccess) return cuda_fail(e, "col_idx");
+    if (val) {
+        if ((e = upload((char**)&d.val, (const char*)val, (size_t)d.nnz * vsize, 8 * vsize, s, bytes)) != cudaSuccess)
+            return cuda_fail(e, "values");
+    }
+    if ((e = upload(&d.tasks, plan.tasks.data(), plan.tasks.size(), 0, s, bytes)) != cudaSuccess)
+        return cuda_fail(e, "tasks");
+    d.n_tasks = (int64_t)plan.tasks.size() - 1;   // the last descriptor is the sentinel
+    if ((e = upload(&d.splits, plan.splits.data(), plan.splits.size(), 0, s, bytes)) != cudaSuccess)
+        return cuda_fail(e, "splits");
+    d.n_splits = (int64_t)plan.splits.size();
+    d.n_segments = plan.n_segments;
+    d.n_slots = plan.n_slots;
+    if (d.n_slots > 0) {
+        size_t pb = (size_t)d.n_slots * kSlotStride * sizeof(float);
+        if ((e = cudaMalloc((void**)&d.partials, pb)) != cudaSuccess) { d.partials = nullptr; return cuda_fail(e, "partials"); }
+        *bytes += (int64_t)pb;
+    }
+    // the plan vectors die with this frame: finish the copies first
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "create sync");
+    return SPMM_OK;
+}
+
+// Defaults for zero fields, then clamp into the ranges the kernels assume
+// (every task's nonzeros fit the staging buffers).
+static Params resolve_params(const spmm_opts* opts) {
+    Params prm;
+    if (opts) {
+        if (opts->task_nnz > 0) prm.task_nnz = opts->task_nnz;
+        if (opts->task_rows > 0) prm.task_rows = opts->task_rows;
+        if (opts->long_row > 0) prm.long_row = opts->long_row;
+        if (opts->short_max > 0) prm.short_max = opts->short_max;
+        if (opts->x_l2_policy == 1) prm.x_evict_last = 0;
+        if (opts->x_l2_policy == 2) prm.x_evict_last = 1;
+    }
+    prm.task_nnz = std::min(std::max(prm.task_nnz, 32), kMaxTaskNnz);
+    prm.task_rows = std::min(std::max(prm.task_rows, 1), kMaxTaskRows);
+    prm.long_row = std::min(std::max(prm.long_row, prm.task_nnz), kMaxTaskNnz);
+    prm.short_max = std::min(std::max(prm.short_max, 1), prm.task_nnz - 1);
+    return prm;
+}
+
+}  // namespace spmm
+
+using namespace spmm;
+
+extern "C" int spmm_plan_tasks(int64_t n_rows, const int64_t* row_ptr, const spmm_opts* opts, int32_t* tasks,
+                               int64_t* n_tasks, int64_t* n_split_rows, int64_t* n_segments) {
+    if (!row_ptr || !n_tasks || n_rows < 0 || n_rows >= (int64_t)1 << 31) {
+        set_error("spmm_plan_tasks: bad argument");
+        return SPMM_ERR_ARG;
+    }
+    if (row_ptr[0] != 0) { set_error("spmm_plan_tasks: row_ptr[0] != 0"); return SPMM_ERR_FORMAT; }
+    for (int64_t i = 0; i < n_rows; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) { set_error("spmm_plan_tasks: row_ptr decreases"); return SPMM_ERR_FORMAT; }
+    HostPlan plan;
+    try {
+        plan = build_plan(row_ptr, n_rows, resolve_params(opts));
+    } catch (const std::bad_alloc&) {
+        set_error("spmm_plan_tasks: out of host memory");
+        return SPMM_ERR_OOM;
+    }
+    const int64_t nt = (int64_t)plan.tasks.size() - 1;
+    if (tasks) {
+        if (*n_tasks < nt) { set_error("spmm_plan_tasks: tasks capacity too small"); return SPMM_ERR_ARG; }
+        std::memcpy(tasks, plan.tasks.data(), plan.tasks.size() * sizeof(int4));
+    }
+    *n_tasks = nt;
+    if (n_split_rows) *n_split_rows = (int64_t)plan.splits.size();
+    if (n_segments) *n_segments = plan.n_segments;
+    return SPMM_OK;
+}
+
+extern "C" const char* spmm_last_error(void) { return g_error.c_str(); }
+
+extern "C" int spmm_create_csr(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, int64_t nnz,
+                               const int64_t* row_ptr, const int32_t* col_idx, const void* values,
+                               spmm_dtype vtype, uint32_t flags, const spmm_opts* opts, void* stream) {
+    set_error("");
+    if (!out) { set_error("spmm_create_csr: out is NULL"); return SPMM_ERR_ARG; }
+    if (n_rows < 0 || n_rows >= (int64_t)1 << 31 || n_cols < 1 || n_cols >= (int64_t)1 << 31 || nnz < 0) {
+        set_error("spmm_create_csr: need 0 <= n_rows < 2^31, 1 <= n_cols < 2^31, nnz >= 0");
+        return SPMM_ERR_ARG;
+    }
+    if (!row_ptr || (nnz > 0 && !col_idx)) { set_error("spmm_create_csr: row_ptr/col_idx is NULL"); return SPMM_ERR_ARG; }
+    if (flags & ~SPMM_WANT_TRANSPOSE) { set_error("spmm_create_csr: unknown flag bits"); return SPMM_ERR_ARG; }
+    size_t vsize = 0;
+    if (values) {
+        if (vtype != SPMM_F32 && vtype != SPMM_BF16 && vtype != SPMM_F16) {
+            set_error("spmm_create_csr: values must be F32, BF16 or F16");
+            return SPMM_ERR_ARG;
+        }
+        vsize = dtype_size(vtype);
+    }
+    // ---- validate the CSR structure
+    if (row_ptr[0] != 0) { set_error("spmm_create_csr: row_ptr[0] != 0"); return SPMM_ERR_FORMAT; }
+    if (row_ptr[n_rows] != nnz) { set_error("spmm_create_csr: row_ptr[n_rows] != nnz"); return SPMM_ERR_FORMAT; }
+    for (int64_t i = 0; i < n_rows; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) {
+            set_error("spmm_create_csr: row_ptr decreases at row " + std::to_string(i));
+            return SPMM_ERR_FORMAT;
+        }
+    for (int64_t p = 0; p < nnz; ++p)
+        if (col_idx[p] < 0 || (int64_t)col_idx[p] >= n_cols) {
+            set_error("spmm_create_csr: column index out of range at entry " + std::to_string(p));
+            return SPMM_ERR_FORMAT;
+        }
+    const Params prm = resolve_params(opts);
+
+    spmm_mat* A = new (std::nothrow) spmm_mat();
+    if (!A) { set_error("spmm_create_csr: out of host memory"); return SPMM_ERR_OOM; }
+    A->params = prm;
+    A->vtype = values ? (int32_t)vtype : -1;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t se = cudaMalloc((void**)&A->status, sizeof(int32_t));
+    if (se == cudaSuccess) se = cudaMemsetAsync(A->status, 0, sizeof(int32_t), s);
+    if (se != cudaSuccess) {
+        cudaFree(A->status);
+        delete A;
+        return cuda_fail(se, "spmm_create_csr: status word");
+    }
+    int rc = build_orientation(A->fwd, n_rows, n_cols, row_ptr, col_idx, values, vsize, prm, s, &A->device_bytes);
+    if (rc == SPMM_OK && (flags & SPMM_WANT_TRANSPOSE)) {
+        // CSR of A^T by a stable counting sort on the column index.
+        std::vector<int64_t> tptr((size_t)n_cols + 1, 0);
+        std::vector<int32_t> tidx;
+        std::vector<char> tval;
+        try {
+            tidx.resize((size_t)nnz);
+            if (values) tval.resize((size_t)nnz * vsize);
+        } catch (const std::bad_alloc&) {
+            rc = SPMM_ERR_OOM;
+            set_error("spmm_create_csr: out of host memory for the transpose");
+        }
+        if (rc == SPMM_OK) {
+            for (int64_t p = 0; p < nnz; ++p) tptr[(size_t)col_idx[p] + 1]++;
+            for (int64_t c = 0; c < n_cols; ++c) tptr[c + 1] += tptr[c];
+            std::vector<int64_t> pos(tptr.begin(), tptr.end() - 1);
+            for (int64_t i = 0; i < n_rows; ++i)
+                for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+                    int64_t q = pos[(size_t)col_idx[p]]++;
+                    tidx[(size_t)q] = (int32_t)i;
+                    if (values) std::memcpy(&tval[(size_t)q * vsize], (const char*)values + p * vsize, vsize);
+                }
+            rc = build_orientation(A->tr, n_cols, n_rows, tptr.data(), tidx.data(), values ? tval.data() : nullptr,
+                                   vsize, prm, s, &A->device_bytes);
+            A->has_tr = (rc == SPMM_OK);
+        }
+    }
+    if (rc != SPMM_OK) {
+        free_dev(A->fwd);
+        free_dev(A->tr);
+        cudaFree(A->status);
+        delete A;
+        return rc;
+    }
+    *out = A;
+    return SPMM_OK;
+}
+
+extern "C" int spmm_apply(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype xtype, void* Y,
+                          int64_t ldy, spmm_dtype ytype, int32_t transpose, void* stream) {
+    if (!A) { set_error("spmm_apply: A is NULL"); return SPMM_ERR_ARG; }
+    if (k < 1 || k > kMaxK) { set_error("spmm_apply: k must be in 1..64"); return SPMM_ERR_ARG; }
+    if (ldx < k || ldy < k) { set_error("spmm_apply: ldx and ldy must be >= k"); return SPMM_ERR_ARG; }
+    if (ytype != SPMM_F32) { set_error("spmm_apply: Y must be F32"); return SPMM_ERR_ARG; }
+    if (xtype != SPMM_F32 && xtype != SPMM_BF16 && xtype != SPMM_F16) {
+        set_error("spmm_apply: X must be F32, BF16 or F16");
+        return SPMM_ERR_ARG;
+    }
+    if (transpose && !A->has_tr) {
+        set_error("spmm_apply: transpose needs SPMM_WANT_TRANSPOSE at create");
+        return SPMM_ERR_ARG;
+    }
+    const DevCSR& d = transpose ? A->tr : A->fwd;
+    if (d.n_rows == 0) return SPMM_OK;
+    if (!X || !Y) { set_error("spmm_apply: X or Y is NULL"); return SPMM_ERR_ARG; }
+    int vmode = 0;
+    if (A->vtype == SPMM_F32) vmode = 1;
+    else if (A->vtype == SPMM_BF16) vmode = 2;
+    else if (A->vtype == SPMM_F16) vmode = 3;
+    if ((vmode == 2 && xtype != SPMM_BF16) || (vmode == 3 && xtype != SPMM_F16)) {
+        set_error("spmm_apply: 16-bit values need X of the same 16-bit type (or use F32 values)");
+        return SPMM_ERR_UNSUPPORTED;
+    }
+    // widest vector that divides k and keeps every X load and Y store aligned
+    const int esize = (int)dtype_size(xtype);
+    const uintptr_t xa = (uintptr_t)X, ya = (uintptr_t)Y;
+    int vec = 16 / esize;
+    for (; vec > 1; vec >>= 1) {
+        const int yv = std::min(vec, 4);
+        if (k % vec == 0 && ldx % vec == 0 && xa % (uintptr_t)(vec * esize) == 0 && ldy % yv == 0 &&
+            ya % (uintptr_t)(yv * 4) == 0)
+            break;
+    }
+    const int nvec = k / vec;
+    const int ch = nvec > 32 ? 2 : 1;
+    const int per = (nvec + ch - 1) / ch;
+    int lg = 0;
+    while ((1 << lg) < per) ++lg;
+
+    FwdArgs a;
+    a.row_ptr = d.row_ptr;
+    a.col_idx = d.col_idx;
+    a.val = d.val;
+    a.tasks = d.tasks;
+    a.n_tasks = d.n_tasks;
+    a.partials = d.partials;
+    a.status = A->status;
+    a.wait_ns = kWaitNs;
+    a.x_evict_last = A->params.x_evict_last;
+    a.X = X;
+    a.ldx = ldx;
+    a.Y = (float*)Y;
+    a.ldy = ldy;
+    a.k = k;
+    a.lanes_log2 = lg;
+    a.nvec = nvec;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (xtype == SPMM_F32) e = launch_rows_f32(a, vmode, vec, ch, s);
+    else if (xtype == SPMM_BF16) e = launch_rows_bf16(a, vmode, vec, ch, s);
+    else e = launch_rows_f16(a, vmode, vec, ch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: row-task kernel");
+    e = launch_combine(d.splits, d.n_splits, d.partials, (float*)Y, ldy, k, s);
+    if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: combine kernel");
+    return SPMM_OK;
+}
+
+extern "C" int spmm_get_info(spmm_mat_t A, spmm_info* info) {
+    if (!A || !info) { set_error("spmm_get_info: NULL argument"); return SPMM_ERR_ARG; }
+    std::memset(info, 0, sizeof(*info));
+    info->n_rows = A->fwd.n_rows;
+    info->n_cols = A->fwd.n_cols;
+    info->nnz = A->fwd.nnz;
+    info->n_tasks = A->fwd.n_tasks;
+    info->n_split_rows = A->fwd.n_splits;
+    info->n_segments = A->fwd.n_segments;
+    if (A->has_tr) {
+        info->n_tasks_t = A->tr.n_tasks;
+        info->n_split_rows_t = A->tr.n_splits;
+        info->n_segments_t = A->tr.n_segments;
+    }
+    info->device_bytes = A->device_bytes;
+    info->value_dtype = A->vtype;
+    info->has_transpose = A->has_tr ? 1 : 0;
+    return SPMM_OK;
+}
+
+extern "C" int spmm_destroy(spmm_mat_t A) {
+    if (!A) return SPMM_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_dev(A->fwd);
+    free_dev(A->tr);
+    cudaFree(A->status);
+    delete A;
+    if (e != cudaSuccess) return cuda_fail(e, "spmm_destroy: pending device work failed");
+    return SPMM_OK;
+}
+
+extern "C" int spmm_sync_status(spmm_mat_t A, void* stream) {
+    if (!A) { set_error("spmm_sync_status: A is NULL"); return SPMM_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "spmm_sync_status: stream");
+    int32_t st = 0;
+    if ((e = cudaMemcpy(&st, A->status, sizeof(st), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "spmm_sync_status: read status");
+    if (st != 0) {
+        cudaMemset(A->status, 0, sizeof(int32_t));
+        set_error("spmm_sync_status: a device-side staging wait timed out; results of the calls since the "
+                  "last check are incomplete");
+        return SPMM_ERR_TIMEOUT;
+    }
+    return SPMM_OK;
+}
+
+extern "C" int spmm_debug_wait_timeout(uint64_t wait_ns, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t* st = nullptr;
+    cudaError_t e = cudaMalloc((void**)&st, sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "spmm_debug_wait_timeout: alloc");
+    int32_t h = 0;
+    if ((e = cudaMemsetAsync(st, 0, sizeof(int32_t), s)) == cudaSuccess &&
+        (e = launch_wait_selftest(st, wait_ns, s)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(&h, st, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    cudaFree(st);
+    if (e != cudaSuccess) return cuda_fail(e, "spmm_debug_wait_timeout");
+    if (h != 0) {
+        set_error("spmm_debug_wait_timeout: the wait ran out as intended");
+        return SPMM_ERR_TIMEOUT;
+    }
+    return SPMM_OK;
+}

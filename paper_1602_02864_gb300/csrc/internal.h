@@ -1,0 +1,120 @@
+// internal.h -- types shared by the host side and the kernels of libspmm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "spmm.h"
+
+namespace spmm {
+
+// Warp tasks, in natural row order, cover every row exactly once:
+//   desc = int4 {r0, x, lo32(e0), hi32(e0)}, e0 = first nonzero of the task,
+//   and the task's nonzero count is e0 of the next descriptor (a sentinel
+//   descriptor closes the list).
+//   x >= 1 : a run of x short rows r0 .. r0+x-1 (one lane group per row)
+//   x == 0 : one long row r0 (all lane groups share its nonzeros)
+//   x < 0  : one segment of a split hub row r0; its partial result goes to
+//            slot -x-1 and combine.cu adds the segments in order.
+//   split  = int4 {row, nseg, slot0, 0} for the combine pass.
+constexpr int kWarpsPerBlock = 8;
+constexpr int kMaxTaskNnz = 512;    // staged nonzeros per task (shared memory)
+constexpr int kMaxTaskRows = 64;    // rows per short-row task
+constexpr int kSlotStride = 64;     // floats per partial-result slot (k <= 64)
+constexpr int kMaxK = 64;
+// per-warp staging buffer (one of two): column indices, values, row pointers,
+// each padded for 16-byte aligned bulk copies of an unaligned window
+constexpr int kColBufInts = kMaxTaskNnz + 8;          // 2080 bytes
+constexpr int kValBufBytes = (kMaxTaskNnz + 8) * 4;   // 2080 bytes
+constexpr int kRpBufLongs = kMaxTaskRows + 4;         // 544 bytes
+
+struct HostPlan {
+    std::vector<int4> tasks;    // n_tasks + 1 (sentinel)
+    std::vector<int4> splits;
+    int64_t n_slots = 0;
+    int64_t n_segments = 0;
+    int64_t n_short = 0, n_long = 0;
+};
+
+// Device-side copy of one orientation (CSR of A, or CSR of A^T == CSC of A).
+struct DevCSR {
+    int64_t n_rows = 0, n_cols = 0, nnz = 0;
+    int64_t* row_ptr = nullptr;     // padded by 2 entries (aligned bulk copies)
+    int32_t* col_idx = nullptr;     // padded by 8 entries
+    void* val = nullptr;            // padded by 8 entries
+    int4* tasks = nullptr;          // n_tasks + 1
+    int64_t n_tasks = 0;
+    int4* splits = nullptr;
+    int64_t n_splits = 0;
+    int64_t n_segments = 0;
+    float* partials = nullptr;      // scratch: n_slots x kSlotStride floats
+    int64_t n_slots = 0;
+};
+
+struct Params {
+    int32_t task_nnz = 256;     // nonzeros per short-row task
+    int32_t task_rows = 64;     // rows per short-row task
+    int32_t long_row = 512;     // rows longer than this are split
+    int32_t short_max = 31;     // rows with more nonzeros are "long"
+    int32_t x_evict_last = 1;   // L2 policy of the X gathers (1 = evict-last)
+};
+
+}  // namespace spmm
+
+struct spmm_mat {
+    spmm::DevCSR fwd;
+    spmm::DevCSR tr;
+    bool has_tr = false;
+    int32_t vtype = -1;       // spmm_dtype of values, -1 = pattern
+    spmm::Params params;
+    int64_t device_bytes = 0;
+    int32_t* status = nullptr;  // device word: nonzero after a timed-out wait
+};
+
+namespace spmm {
+
+// plan.cpp
+HostPlan build_plan(const int64_t* row_ptr, int64_t n_rows, const Params& p);
+
+// abi.cu
+void set_error(const std::string& msg);
+
+// Arguments of the task kernel (one instantiation per x type / value type /
+// vector width / column chunks).
+struct FwdArgs {
+    const int64_t* row_ptr;
+    const int32_t* col_idx;
+    const void* val;
+    const int4* tasks;
+    int64_t n_tasks;
+    float* partials;
+    const void* X;
+    int64_t ldx;
+    float* Y;
+    int64_t ldy;
+    int32_t k;
+    int32_t lanes_log2;   // log2(lanes per nonzero)
+    int32_t nvec;         // k / VEC vectors per X row
+    int32_t* status;      // set to 1 if a staging wait times out
+    uint64_t wait_ns;     // bound of every staging wait
+    int32_t x_evict_last; // gather X with the L2 evict-last policy
+};
+
+// rows_*.cu: launch the task kernel for one X dtype.  vmode: 0 pattern,
+// 1 f32 values, 2 bf16 values, 3 f16 values.  Returns a cudaError_t.
+cudaError_t launch_rows_f32(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
+cudaError_t launch_rows_bf16(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
+cudaError_t launch_rows_f16(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
+
+// combine.cu: Y[row] = sum of the split row's partials in segment order.
+cudaError_t launch_combine(const int4* splits, int64_t n_splits, const float* partials, float* Y,
+                           int64_t ldy, int32_t k, cudaStream_t s);
+
+// status.cu: a kernel whose staging wait can never complete, to exercise
+// the bounded-wait error path.
+cudaError_t launch_wait_selftest(int32_t* status, uint64_t wait_ns, cudaStream_t s);
+
+}  // namespace spmm

@@ -1,0 +1,67 @@
+// plan.cpp -- host-side warp-task plan for one CSR orientation.
+//
+// The paper's executor (Section 3.4, Algorithm 1) hands threads batches of
+// whole tile rows from a global queue and keeps each output row owned by one
+// thread (horizontal partitioning), so no output row is written twice and the
+// load stays balanced.  Here the unit is a warp task, and rows are binned by
+// degree (the GPU analogue of the paper's tile-row batches and of its COO
+// section for single-entry rows, Section 3.2):
+//   - short rows (degree <= short_max, including empty and degree-1/2 rows)
+//     are packed in runs of consecutive rows, at most task_rows rows and
+//     task_nnz nonzeros per task; each lane group of the warp owns whole rows;
+//   - a long row (short_max < degree <= long_row) is one task whose nonzeros
+//     are shared by all lane groups of the warp;
+//   - a hub row (degree > long_row) is split into segments of about task_nnz
+//     nonzeros, one task each; every segment writes a partial result and a
+//     second pass adds the partials in segment order.
+// Tasks keep the natural row order, so a task reads contiguous slices of the
+// row pointers and column indices and writes a contiguous block of Y.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace spmm {
+
+static int4 desc(int64_t r0, int32_t x, int64_t e0) {
+    return make_int4((int)r0, x, (int)(uint32_t)(e0 & 0xffffffffll), (int)(e0 >> 32));
+}
+
+HostPlan build_plan(const int64_t* row_ptr, int64_t n_rows, const Params& p) {
+    HostPlan plan;
+    const int64_t T = p.task_nnz, R = p.task_rows, LR = p.long_row, SM = p.short_max;
+    plan.tasks.reserve((size_t)(row_ptr[n_rows] / T + n_rows / R + 16));
+    int64_t r = 0;
+    while (r < n_rows) {
+        const int64_t d = row_ptr[r + 1] - row_ptr[r];
+        if (d > SM) {
+            if (d > LR) {
+                const int64_t nseg = (d + T - 1) / T;
+                const int64_t seglen = (d + nseg - 1) / nseg;
+                plan.splits.push_back(make_int4((int)r, (int)nseg, (int)plan.n_slots, 0));
+                for (int64_t s = 0; s < nseg; ++s)
+                    plan.tasks.push_back(desc(r, (int32_t)(-(plan.n_slots + s) - 1), row_ptr[r] + s * seglen));
+                plan.n_slots += nseg;
+                plan.n_segments += nseg;
+            } else {
+                plan.tasks.push_back(desc(r, 0, row_ptr[r]));
+                ++plan.n_long;
+            }
+            ++r;
+            continue;
+        }
+        const int64_t r0 = r;
+        int64_t nnz = 0;
+        while (r < n_rows && r - r0 < R) {
+            const int64_t dr = row_ptr[r + 1] - row_ptr[r];
+            if (dr > SM || nnz + dr > T) break;
+            nnz += dr;
+            ++r;
+        }
+        plan.tasks.push_back(desc(r0, (int32_t)(r - r0), row_ptr[r0]));
+        ++plan.n_short;
+    }
+    plan.tasks.push_back(desc(n_rows, 0, row_ptr[n_rows]));   // sentinel
+    return plan;
+}
+
+}  // namespace spmm

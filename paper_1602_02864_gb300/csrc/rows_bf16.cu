@@ -1,0 +1,11 @@
+// rows_bf16.cu -- row-task kernel instantiations for __nv_bfloat16 X (split per dtype so
+// the translation units compile in parallel).
+#include "rows_kernel.cuh"
+
+namespace spmm {
+
+cudaError_t launch_rows_bf16(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
+    return launch_rows_t<__nv_bfloat16>(a, vmode, vec, ch, s);
+}
+
+}  // namespace spmm

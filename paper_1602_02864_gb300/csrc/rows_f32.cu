@@ -1,0 +1,11 @@
+// rows_f32.cu -- row-task kernel instantiations for float X (split per dtype so
+// the translation units compile in parallel).
+#include "rows_kernel.cuh"
+
+namespace spmm {
+
+cudaError_t launch_rows_f32(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
+    return launch_rows_t<float>(a, vmode, vec, ch, s);
+}
+
+}  // namespace spmm

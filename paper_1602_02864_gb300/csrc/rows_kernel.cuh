@@ -1,0 +1,496 @@
+// rows_kernel.cuh -- the SpMM task kernel, Y = A X for one CSR orientation.
+//
+// Section 3.4 / Algorithm 1 of the paper: a nonzero a_ij scales the whole
+// dense row X[j, :] into output row i, the row operation is vectorised (AVX
+// in the paper, 16-byte lane loads here), and each output row has a single
+// owner.
+//
+// Persistent warps walk the task list (plan.cpp) with a stride of the grid's
+// warp count.  Each warp stages a task's column indices, values and row
+// pointers into shared memory with bulk asynchronous copies (cp.async.bulk,
+// completion on an mbarrier) one task ahead, so the copy of task i+1 overlaps
+// the gathers of task i -- the GPU form of the paper's asynchronous tile-row
+// reads (Algorithm 1: read the tile rows asynchronously, multiply once they
+// have arrived).  Every wait on a copy is bounded; on timeout the warp sets a
+// status word, waits (bounded) for its other copy and exits.
+//
+// A warp is cut into G = 32 / LANES lane groups; LANES lanes cover one X row
+// (each lane VEC consecutive elements, CH chunks of them).
+//   short-row task: group g owns rows g, g+G, ... of the run and sums each
+//                   row's nonzeros in order;
+//   long row / hub segment: group g takes nonzeros g, g+G, g+2G, ...; the
+//                   groups' partial sums are added by a fixed xor-shuffle
+//                   tree; a segment writes its sum to a partial slot.
+// All summation orders are fixed, so repeated calls give identical results.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
+#include "internal.h"
+
+namespace spmm {
+
+// ------------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared; both addresses 16-byte aligned, bytes % 16
+// == 0.  `policy` is an L2 cache policy (the streamed matrix is marked
+// evict-first so it does not push the gathered X rows out of L2).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                         uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// read-only global loads with an L2 cache policy
+__device__ __forceinline__ float4 ldg_f4(const float* p, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float2 ldg_f2(const float* p, uint64_t pol) {
+    float2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ldg_f1(const float* p, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint4 ldg_u4(const void* p, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint2 ldg_u2(const void* p, uint64_t pol) {
+    uint2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint32_t ldg_u1(const void* p, uint64_t pol) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint32_t ldg_u16(const void* p, uint64_t pol) {
+    unsigned short v;
+    asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for phase `parity` of `bar`; false if it did not complete within limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// ------------------------------------------------------- element loading --
+template <typename XT>
+__device__ __forceinline__ float bits_to_f32(uint32_t b);
+template <>
+__device__ __forceinline__ float bits_to_f32<__nv_bfloat16>(uint32_t b) {
+    return __uint_as_float(b << 16);
+}
+template <>
+__device__ __forceinline__ float bits_to_f32<__half>(uint32_t b) {
+    return __half2float(__ushort_as_half((unsigned short)b));
+}
+
+// VEC consecutive elements of X held as loaded (16-bit types stay packed two
+// per 32-bit word until they are used, which halves the registers that hold
+// loads in flight).  p is aligned to VEC * sizeof(XT).
+template <typename XT, int VEC>
+struct XVec {
+    static_assert(sizeof(XT) == 2, "16-bit element path");
+    static constexpr int kWords = (VEC + 1) / 2;
+    uint32_t w[kWords];
+    __device__ __forceinline__ void load(const XT* p, uint64_t pol) {
+        if constexpr (VEC == 8) {
+            uint4 v = ldg_u4(p, pol);
+            w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+        } else if constexpr (VEC == 4) {
+            uint2 v = ldg_u2(p, pol);
+            w[0] = v.x; w[1] = v.y;
+        } else if constexpr (VEC == 2) {
+            w[0] = ldg_u1(p, pol);
+        } else {
+            w[0] = ldg_u16(p, pol);
+        }
+    }
+    __device__ __forceinline__ float get(int i) const {
+        return bits_to_f32<XT>((i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xffffu));
+    }
+};
+
+template <int VEC>
+struct XVec<float, VEC> {
+    float f[VEC];
+    __device__ __forceinline__ void load(const float* p, uint64_t pol) {
+        if constexpr (VEC == 4) {
+            float4 v = ldg_f4(p, pol);
+            f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w;
+        } else if constexpr (VEC == 2) {
+            float2 v = ldg_f2(p, pol);
+            f[0] = v.x; f[1] = v.y;
+        } else {
+            f[0] = ldg_f1(p, pol);
+        }
+    }
+    __device__ __forceinline__ float get(int i) const { return f[i]; }
+};
+
+// Store VEC floats to an address aligned to min(VEC, 4) * 4 bytes.
+template <int VEC>
+__device__ __forceinline__ void store_y(float* p, const float (&v)[VEC]) {
+    if constexpr (VEC >= 4) {
+#pragma unroll
+        for (int i = 0; i < VEC; i += 4)
+            __stcs(reinterpret_cast<float4*>(p + i), make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
+    } else if constexpr (VEC == 2) {
+        __stcs(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
+    } else {
+        __stcs(p, v[0]);
+    }
+}
+
+// value of staged entry i (shared memory, raw bytes of the stored type)
+template <int VMODE>
+__device__ __forceinline__ float staged_val(const unsigned char* v, int i) {
+    if constexpr (VMODE == 1) return reinterpret_cast<const float*>(v)[i];
+    if constexpr (VMODE == 2) return __uint_as_float((uint32_t)reinterpret_cast<const unsigned short*>(v)[i] << 16);
+    if constexpr (VMODE == 3) return __half2float(__ushort_as_half(reinterpret_cast<const unsigned short*>(v)[i]));
+    return 1.0f;
+}
+
+template <int VMODE>
+struct Layout {
+    static constexpr int kValBytes = VMODE == 0 ? 0 : (VMODE == 1 ? 4 : 2);
+    static constexpr int kColOff = 0;
+    static constexpr int kValOff = kColBufInts * 4;
+    static constexpr int kRpOff = kValOff + (VMODE ? kValBufBytes : 0);
+    static constexpr int kBuf = kRpOff + kRpBufLongs * 8;       // bytes per staging buffer
+    static constexpr int kWarp = 2 * kBuf + 16;                 // two buffers + two mbarriers
+    static constexpr int kBlock = kWarpsPerBlock * kWarp;
+    static_assert(kBuf % 16 == 0 && kWarp % 16 == 0, "16-byte aligned staging buffers");
+};
+
+struct Staged {
+    const int32_t* col;         // col[i] = column of nonzero e0 + i
+    const unsigned char* val;   // raw value bytes, entry i = nonzero e0 + i
+    const int64_t* rp;          // rp[j] = row_ptr[r0 + j] (short-row tasks)
+};
+
+__device__ __forceinline__ int64_t desc_e0(const int4 d) {
+    return ((int64_t)(uint32_t)d.z) | ((int64_t)d.w << 32);
+}
+
+// Issue the bulk copies of one task into staging buffer `buf` (lane 0 only).
+// Windows are widened to 16-byte boundaries; the arrays are padded on the
+// device so the widened end stays inside the allocation.
+template <int VMODE>
+__device__ __forceinline__ void issue_task(const FwdArgs& a, const int4 d0, const int4 d1, unsigned char* buf,
+                                           uint64_t* bar, uint64_t pol) {
+    using Lay = Layout<VMODE>;
+    const int64_t e0 = desc_e0(d0), e1 = desc_e0(d1);
+    const int64_t cs = e0 & ~(int64_t)3, ce = (e1 + 3) & ~(int64_t)3;
+    const uint32_t cbytes = (uint32_t)((ce - cs) * 4);
+    uint32_t vbytes = 0, rbytes = 0;
+    int64_t vs = 0, rs = 0;
+    if constexpr (VMODE != 0) {
+        constexpr int epb = 16 / Lay::kValBytes;
+        vs = e0 & ~(int64_t)(epb - 1);
+        const int64_t ve = (e1 + epb - 1) & ~(int64_t)(epb - 1);
+        vbytes = (uint32_t)((ve - vs) * Lay::kValBytes);
+    }
+    if (d0.y > 0) {
+        rs = (int64_t)d0.x & ~(int64_t)1;
+        const int64_t re = ((int64_t)d0.x + d0.y + 2) & ~(int64_t)1;
+        rbytes = (uint32_t)((re - rs) * 8);
+    }
+    mbar_arrive_expect_tx(bar, cbytes + vbytes + rbytes);
+    if (cbytes) bulk_g2s(buf + Lay::kColOff, a.col_idx + cs, cbytes, bar, pol);
+    if constexpr (VMODE != 0)
+        if (vbytes)
+            bulk_g2s(buf + Lay::kValOff, reinterpret_cast<const unsigned char*>(a.val) + vs * Lay::kValBytes, vbytes,
+                     bar, pol);
+    if (rbytes) bulk_g2s(buf + Lay::kRpOff, a.row_ptr + rs, rbytes, bar, pol);
+}
+
+#ifndef SPMM_UNROLL_BYTES
+#define SPMM_UNROLL_BYTES 64      // X bytes in flight per lane
+#endif
+#ifndef SPMM_MIN_BLOCKS
+#define SPMM_MIN_BLOCKS 4         // resident blocks per SM the register budget targets
+#endif
+
+template <typename XT, int VMODE, int VEC, int CH>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOCKS) rows_kernel(FwdArgs a) {
+    using Lay = Layout<VMODE>;
+    // nonzeros in flight per lane group
+    constexpr int kBytes = VEC * CH * (int)sizeof(XT);
+    constexpr int kU = SPMM_UNROLL_BYTES / kBytes;
+    constexpr int U = kU < 2 ? 2 : (kU > 16 ? 16 : kU);
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* wb = smem + w * Lay::kWarp;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wb + 2 * Lay::kBuf);
+
+    const int64_t W = (int64_t)gridDim.x * kWarpsPerBlock;
+    int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+    if (t >= a.n_tasks) return;
+    if (lane == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+
+    // lane geometry
+    const int lg = a.lanes_log2;
+    const int LANES = 1 << lg, G = 32 >> lg;
+    const int g = lane >> lg, li = lane & (LANES - 1);
+    bool act[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) act[c] = (li + c * LANES) < a.nvec;
+    const XT* xb = reinterpret_cast<const XT*>(a.X) + (int64_t)li * VEC;
+
+    const uint64_t apol = policy_evict_first();
+    const uint64_t xpol = a.x_evict_last ? policy_evict_last() : policy_evict_normal();
+    int4 d0 = a.tasks[t], d1 = a.tasks[t + 1];
+    if (lane == 0) issue_task<VMODE>(a, d0, d1, wb, &bars[0], apol);
+    int64_t tn = t + W;
+    int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
+    if (tn < a.n_tasks) { n0 = a.tasks[tn]; n1 = a.tasks[tn + 1]; }
+    uint32_t phase = 0;     // bit b = parity to wait for on buffer b
+    int b = 0;
+
+    for (;;) {
+        // stage the next task into the other buffer (its readers are done)
+        if (tn < a.n_tasks) {
+            __syncwarp();
+            if (lane == 0) {
+                fence_proxy_async();
+                issue_task<VMODE>(a, n0, n1, wb + (b ^ 1) * Lay::kBuf, &bars[b ^ 1], apol);
+            }
+        }
+        // prefetch the descriptor after next
+        const int64_t tnn = tn + W;
+        int4 m0 = make_int4(0, 0, 0, 0), m1 = m0;
+        if (tnn < a.n_tasks) { m0 = a.tasks[tnn]; m1 = a.tasks[tnn + 1]; }
+
+        if (!mbar_wait_bounded(&bars[b], (phase >> b) & 1u, a.wait_ns)) {
+            if (lane == 0) atomicExch(a.status, 1);
+            if (tn < a.n_tasks) mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u, a.wait_ns);
+            return;
+        }
+        phase ^= 1u << b;
+
+        // ---- compute task (d0, d1) from buffer b
+        {
+            const unsigned char* buf = wb + b * Lay::kBuf;
+            const int64_t e0 = desc_e0(d0);
+            const int n = (int)(desc_e0(d1) - e0);
+            Staged st;
+            st.col = reinterpret_cast<const int32_t*>(buf + Lay::kColOff) + (e0 & 3);
+            if constexpr (VMODE != 0) {
+                constexpr int epb = 16 / Lay::kValBytes;
+                st.val = buf + Lay::kValOff + (e0 & (epb - 1)) * Lay::kValBytes;
+            } else {
+                st.val = nullptr;
+            }
+            st.rp = reinterpret_cast<const int64_t*>(buf + Lay::kRpOff) + (d0.x & 1);
+
+            if (d0.y > 0) {
+                // run of short rows: lane group g owns rows g, g+G, ...
+                const int nr = d0.y;
+                for (int j = g; j < nr; j += G) {
+                    const int s = (int)(st.rp[j] - e0), e = (int)(st.rp[j + 1] - e0);
+                    float acc[CH][VEC];
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[c][v] = 0.f;
+                    for (int i = s; i < e; i += U) {
+                        XVec<XT, VEC> xv[U][CH];
+                        float av[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (i + u < e) {
+                                const int64_t cidx = st.col[i + u];
+                                av[u] = staged_val<VMODE>(st.val, i + u);
+#pragma unroll
+                                for (int c = 0; c < CH; ++c)
+                                    if (act[c]) xv[u][c].load(xb + cidx * a.ldx + c * LANES * VEC, xpol);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            if (i + u < e) {
+#pragma unroll
+                                for (int c = 0; c < CH; ++c)
+#pragma unroll
+                                    for (int v = 0; v < VEC; ++v) acc[c][v] = fmaf(av[u], xv[u][c].get(v), acc[c][v]);
+                            }
+                    }
+                    float* dst = a.Y + (int64_t)(d0.x + j) * a.ldy;
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+                        if (act[c]) store_y<VEC>(dst + (li + c * LANES) * VEC, acc[c]);
+                }
+            } else {
+                // one long row or one hub segment: nonzeros g, g+G, ... per group
+                float acc[CH][VEC];
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[c][v] = 0.f;
+                for (int i = g; i < n; i += G * U) {
+                    XVec<XT, VEC> xv[U][CH];
+                    float av[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int idx = i + u * G;
+                        if (idx < n) {
+                            const int64_t cidx = st.col[idx];
+                            av[u] = staged_val<VMODE>(st.val, idx);
+#pragma unroll
+                            for (int c = 0; c < CH; ++c)
+                                if (act[c]) xv[u][c].load(xb + cidx * a.ldx + c * LANES * VEC, xpol);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (i + u * G < n) {
+#pragma unroll
+                            for (int c = 0; c < CH; ++c)
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) acc[c][v] = fmaf(av[u], xv[u][c].get(v), acc[c][v]);
+                        }
+                }
+                for (int off = LANES; off < 32; off <<= 1)
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[c][v] += __shfl_xor_sync(0xffffffffu, acc[c][v], off);
+                if (g == 0) {
+                    float* dst = (d0.y == 0) ? a.Y + (int64_t)d0.x * a.ldy
+                                             : a.partials + (int64_t)(-d0.y - 1) * kSlotStride;
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+                        if (act[c]) store_y<VEC>(dst + (li + c * LANES) * VEC, acc[c]);
+                }
+            }
+        }
+        if (tn >= a.n_tasks) break;
+        d0 = n0; d1 = n1;
+        n0 = m0; n1 = m1;
+        tn = tnn;
+        b ^= 1;
+    }
+}
+
+template <typename XT, int VMODE, int VEC, int CH>
+cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
+    using Lay = Layout<VMODE>;
+    static int blocks_per_sm = 0;   // per instantiation, computed once
+    static int num_sms = 0;
+    if (blocks_per_sm == 0) {
+        cudaError_t e;
+        if (Lay::kBlock > 48 * 1024) {
+            e = cudaFuncSetAttribute(rows_kernel<XT, VMODE, VEC, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     Lay::kBlock);
+            if (e != cudaSuccess) return e;
+        }
+        int dev = 0, nb = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rows_kernel<XT, VMODE, VEC, CH>,
+                                                               kWarpsPerBlock * 32, Lay::kBlock)) != cudaSuccess)
+            return e;
+        num_sms = sms;
+        blocks_per_sm = nb > 0 ? nb : 1;
+    }
+    const int64_t want = (a.n_tasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int64_t cap = (int64_t)blocks_per_sm * num_sms;
+    const dim3 grid((unsigned)(want < cap ? want : cap));
+    rows_kernel<XT, VMODE, VEC, CH><<<grid, kWarpsPerBlock * 32, Lay::kBlock, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename XT>
+cudaError_t launch_rows_t(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
+    if (a.n_tasks <= 0) return cudaSuccess;
+#define SPMM_LAUNCH(VM, V, C) \
+    if (vmode == VM && vec == V && ch == C) return launch_one<XT, VM, V, C>(a, s);
+    if constexpr (sizeof(XT) == 4) {
+        SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1) SPMM_LAUNCH(0, 1, 2)
+        SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1) SPMM_LAUNCH(1, 1, 2)
+    } else {
+        constexpr int VM3 = std::is_same<XT, __half>::value ? 3 : 2;  // own-type values
+        SPMM_LAUNCH(0, 8, 1) SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1) SPMM_LAUNCH(0, 1, 2)
+        SPMM_LAUNCH(1, 8, 1) SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1) SPMM_LAUNCH(1, 1, 2)
+        SPMM_LAUNCH(VM3, 8, 1) SPMM_LAUNCH(VM3, 4, 1) SPMM_LAUNCH(VM3, 2, 1) SPMM_LAUNCH(VM3, 1, 1)
+        SPMM_LAUNCH(VM3, 1, 2)
+    }
+#undef SPMM_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace spmm

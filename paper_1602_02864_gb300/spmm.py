@@ -1,0 +1,230 @@
+"""ctypes binding of libspmm.so (include/spmm.h).  Argument marshalling only:
+every step of the computation runs in the library's CUDA kernels.  Importing
+this module fails loudly if the compiled library is missing -- there is no CPU
+fallback.
+
+Functions keep the C names (``spmm_create_csr``, ``spmm_apply``, ...);
+``SparseMatrix`` is a small convenience wrapper around a handle that accepts
+numpy arrays for A and torch CUDA tensors for X and Y.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspmm.so")
+
+SPMM_F32, SPMM_BF16, SPMM_F16, SPMM_F64 = 0, 1, 2, 3
+SPMM_OK = 0
+SPMM_ERR_ARG, SPMM_ERR_CUDA, SPMM_ERR_OOM, SPMM_ERR_FORMAT, SPMM_ERR_TIMEOUT, SPMM_ERR_UNSUPPORTED = (
+    -1, -2, -3, -4, -5, -6)
+SPMM_WANT_TRANSPOSE = 0x1
+
+_STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_FORMAT", -5: "ERR_TIMEOUT",
+           -6: "ERR_UNSUPPORTED"}
+
+
+class SpmmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class spmm_opts(ctypes.Structure):
+    _fields_ = [("task_nnz", ctypes.c_int32), ("task_rows", ctypes.c_int32), ("long_row", ctypes.c_int32),
+                ("short_max", ctypes.c_int32), ("x_l2_policy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class spmm_info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("n_rows", "n_cols", "nnz", "n_tasks", "n_split_rows", "n_segments",
+                                              "n_tasks_t", "n_split_rows_t", "n_segments_t", "device_bytes")] + [
+        ("value_dtype", ctypes.c_int32), ("has_transpose", ctypes.c_int32)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+                      "(the library has no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P = ctypes.c_void_p
+_i32, _i64, _u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+
+_lib.spmm_create_csr.argtypes = [ctypes.POINTER(_P), _i64, _i64, _i64, _P, _P, _P, ctypes.c_int, _u32,
+                                 ctypes.POINTER(spmm_opts), _P]
+_lib.spmm_create_csr.restype = ctypes.c_int
+_lib.spmm_apply.argtypes = [_P, _P, _i64, _i32, ctypes.c_int, _P, _i64, ctypes.c_int, _i32, _P]
+_lib.spmm_apply.restype = ctypes.c_int
+_lib.spmm_get_info.argtypes = [_P, ctypes.POINTER(spmm_info)]
+_lib.spmm_get_info.restype = ctypes.c_int
+_lib.spmm_destroy.argtypes = [_P]
+_lib.spmm_destroy.restype = ctypes.c_int
+_lib.spmm_sync_status.argtypes = [_P, _P]
+_lib.spmm_sync_status.restype = ctypes.c_int
+_lib.spmm_debug_wait_timeout.argtypes = [ctypes.c_uint64, _P]
+_lib.spmm_debug_wait_timeout.restype = ctypes.c_int
+_lib.spmm_plan_tasks.argtypes = [_i64, _P, ctypes.POINTER(spmm_opts), _P, ctypes.POINTER(_i64),
+                                 ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+_lib.spmm_plan_tasks.restype = ctypes.c_int
+_lib.spmm_last_error.argtypes = []
+_lib.spmm_last_error.restype = ctypes.c_char_p
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def spmm_last_error() -> str:
+    return _lib.spmm_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != SPMM_OK:
+        raise SpmmError(rc, spmm_last_error())
+
+
+def _ptr(a) -> _P:
+    if a is None:
+        return _P(0)
+    if isinstance(a, np.ndarray):
+        return _P(a.ctypes.data)
+    return _P(a.data_ptr())   # torch tensor
+
+
+def _torch_dtype_code(t) -> int:
+    import torch
+    return {torch.float32: SPMM_F32, torch.bfloat16: SPMM_BF16, torch.float16: SPMM_F16,
+            torch.float64: SPMM_F64}[t.dtype]
+
+
+def _np_dtype_code(a) -> int:
+    if a.dtype == np.float32:
+        return SPMM_F32
+    if a.dtype == np.float16:
+        return SPMM_F16
+    raise TypeError("host values must be float32 or float16 numpy arrays (bf16: pass a torch CPU tensor)")
+
+
+def _stream_handle(stream) -> _P:
+    if stream is None:
+        import torch
+        return _P(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _P(stream)
+    return _P(stream.cuda_stream)
+
+
+def spmm_create_csr(n_rows, n_cols, row_ptr, col_idx, values=None, flags=0, opts: spmm_opts | None = None,
+                    stream=None) -> _P:
+    """Returns a handle (c_void_p).  row_ptr/col_idx/values are host arrays."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    vtype = SPMM_F32
+    vptr = _P(0)
+    vkeep = None
+    if values is not None:
+        try:
+            import torch
+            if isinstance(values, torch.Tensor):
+                vkeep = values.contiguous().cpu()
+                vtype = _torch_dtype_code(vkeep)
+                vptr = _P(vkeep.data_ptr())
+        except ImportError:  # pragma: no cover
+            pass
+        if vkeep is None:
+            vkeep = np.ascontiguousarray(values)
+            vtype = _np_dtype_code(vkeep)
+            vptr = _P(vkeep.ctypes.data)
+    h = _P(0)
+    _check(_lib.spmm_create_csr(ctypes.byref(h), int(n_rows), int(n_cols), int(rp[-1]) if len(rp) else 0,
+                                _ptr(rp), _ptr(ci), vptr, vtype, int(flags),
+                                ctypes.byref(opts) if opts is not None else None, _stream_handle(stream)))
+    return h
+
+
+def spmm_apply(h, X, ldx, k, xtype, Y, ldy, transpose=0, stream=None):
+    _check(_lib.spmm_apply(h, _ptr(X), int(ldx), int(k), int(xtype), _ptr(Y), int(ldy), SPMM_F32,
+                           int(transpose), _stream_handle(stream)))
+
+
+def spmm_sync_status(h, stream=None):
+    """Raise SpmmError(SPMM_ERR_TIMEOUT) if a device-side wait ran out."""
+    _check(_lib.spmm_sync_status(h, _stream_handle(stream)))
+
+
+def spmm_debug_wait_timeout(wait_ns: int, stream=None) -> int:
+    """Run the never-completing bounded wait; returns the status code."""
+    return _lib.spmm_debug_wait_timeout(int(wait_ns), _stream_handle(stream))
+
+
+def spmm_plan_tasks(row_ptr, opts: spmm_opts | None = None):
+    """Host-only plan of a row-pointer array: returns (tasks int32 [n+1, 4],
+    n_split_rows, n_segments)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    n_rows = len(rp) - 1
+    nt, ns, nseg = _i64(0), _i64(0), _i64(0)
+    o = ctypes.byref(opts) if opts is not None else None
+    _check(_lib.spmm_plan_tasks(n_rows, _ptr(rp), o, None, ctypes.byref(nt), ctypes.byref(ns), ctypes.byref(nseg)))
+    tasks = np.zeros((nt.value + 1, 4), dtype=np.int32)
+    _check(_lib.spmm_plan_tasks(n_rows, _ptr(rp), o, _ptr(tasks), ctypes.byref(nt), ctypes.byref(ns),
+                                ctypes.byref(nseg)))
+    return tasks, ns.value, nseg.value
+
+
+def spmm_get_info(h) -> dict:
+    info = spmm_info()
+    _check(_lib.spmm_get_info(h, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in info._fields_}
+
+
+def spmm_destroy(h):
+    _check(_lib.spmm_destroy(h))
+
+
+class SparseMatrix:
+    """A sparse matrix resident in HBM: ``SparseMatrix(A_csr).apply(X)``."""
+
+    def __init__(self, n_rows, n_cols, row_ptr, col_idx, values=None, transpose=False,
+                 opts: spmm_opts | None = None, stream=None):
+        self.n_rows, self.n_cols = int(n_rows), int(n_cols)
+        self.handle = spmm_create_csr(n_rows, n_cols, row_ptr, col_idx, values,
+                                      SPMM_WANT_TRANSPOSE if transpose else 0, opts, stream)
+
+    @classmethod
+    def from_csr(cls, A, transpose=False, values=None, **kw):
+        vals = A.values if values is None else values
+        return cls(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, vals, transpose=transpose, **kw)
+
+    def apply(self, X, transpose=False, Y=None, stream=None):
+        """Y = A X (or A^T X).  X: 2-D CUDA tensor (float32/bfloat16/float16)
+        with unit column stride; returns / fills a float32 CUDA tensor."""
+        import torch
+        if X.dim() != 2 or X.stride(1) != 1:
+            raise ValueError("X must be 2-D with unit column stride")
+        k = X.shape[1]
+        out_rows = self.n_cols if transpose else self.n_rows
+        if Y is None:
+            Y = torch.empty((out_rows, k), dtype=torch.float32, device=X.device)
+        if Y.dim() != 2 or Y.stride(1) != 1 or Y.dtype != torch.float32:
+            raise ValueError("Y must be a 2-D float32 tensor with unit column stride")
+        spmm_apply(self.handle, X, X.stride(0), k, _torch_dtype_code(X), Y, Y.stride(0), int(transpose), stream)
+        return Y
+
+    def info(self) -> dict:
+        return spmm_get_info(self.handle)
+
+    def sync_status(self, stream=None):
+        spmm_sync_status(self.handle, stream)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            spmm_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

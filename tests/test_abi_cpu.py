@@ -1,0 +1,64 @@
+"""CPU-side checks of the C-ABI library: it builds for sm_103a, loads, exports
+every function include/spmm.h declares, and rejects malformed input on the
+host before touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(spmm_\w+)\s*\(", src, flags=re.M)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1602_02864_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("spmm_create_csr", "spmm_apply", "spmm_destroy", "spmm_last_error", "spmm_get_info"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_validation_without_gpu(lib):
+    from paper_1602_02864_gb300 import spmm as sp
+    h = ctypes.c_void_p(0)
+    rp = np.array([0, 2, 1, 3], dtype=np.int64)       # decreasing row pointer
+    ci = np.array([0, 1, 2], dtype=np.int32)
+    rc = lib.spmm_create_csr(ctypes.byref(h), ctypes.c_int64(3), ctypes.c_int64(3), ctypes.c_int64(3),
+                             ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(ci.ctypes.data), None, 0, 0, None,
+                             None)
+    assert rc == sp.SPMM_ERR_FORMAT and not h.value
+    assert b"decreases" in sp.lib().spmm_last_error() or "decreases" in sp.spmm_last_error()
+    rp = np.array([0, 1, 2, 3], dtype=np.int64)
+    ci = np.array([0, 5, 2], dtype=np.int32)           # column out of range
+    rc = lib.spmm_create_csr(ctypes.byref(h), ctypes.c_int64(3), ctypes.c_int64(3), ctypes.c_int64(3),
+                             ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(ci.ctypes.data), None, 0, 0, None,
+                             None)
+    assert rc == sp.SPMM_ERR_FORMAT
+    rc = lib.spmm_create_csr(None, ctypes.c_int64(3), ctypes.c_int64(3), ctypes.c_int64(3),
+                             ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(ci.ctypes.data), None, 0, 0, None,
+                             None)
+    assert rc == sp.SPMM_ERR_ARG
+    assert lib.spmm_destroy(None) == 0

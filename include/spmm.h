@@ -168,6 +168,44 @@ int spmm_debug_wait_timeout(uint64_t wait_ns, void* stream);
 int spmm_plan_tasks(int64_t n_rows, const int64_t* row_ptr, const spmm_opts* opts, int32_t* tasks,
                     int64_t* n_tasks, int64_t* n_split_rows, int64_t* n_segments);
 
+/*
+ * spmm_apply_csr_static -- Y = A X without allocating device memory.  The
+ * paper has no counterpart; this exists for callers that cannot call
+ * cudaMalloc (for example code inside a framework that hands out all device
+ * memory from its own pool, or a loop that must not allocate after start-up)
+ * and so cannot create a handle.  The caller passes the matrix, its plan, X
+ * and Y in device buffers it owns; the kernels' scratch (partial sums of
+ * split hub rows, the bounded-wait status word) comes from one static device
+ * array of 4 MiB inside the library, which every GPU that loads the library
+ * keeps until the process exits.
+ *   n_rows, n_cols, nnz   matrix shape and stored entries
+ *   row_ptr   device, n_rows+1 int64; must stay readable 16 bytes past its end
+ *   col_idx   device, nnz int32; must stay readable 32 bytes past its end
+ *   values    device, nnz values of type vtype, or NULL (pattern); readable
+ *             32 bytes past its end.  F32 values, or BF16/F16 values with X of
+ *             the same type.  (The kernel's bulk copies are widened to 16-byte
+ *             boundaries; the extra bytes are read but not used.)
+ *   tasks     device copy of the n_tasks + 1 descriptors (sentinel included)
+ *             that spmm_plan_tasks returned for this row_ptr
+ *   n_tasks, n_segments   as returned by spmm_plan_tasks; at most 16384
+ *             segments (split hub-row pieces) fit the static scratch
+ *   X, ldx, k, xtype, Y, ldy   as for spmm_apply (Y float32, device)
+ * The result equals spmm_apply on a handle created from the same matrix and
+ * options.  The first call on a device looks up the static array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the array and it keeps
+ * the last call's contents: calls whose work overlaps on the GPU race, so
+ * order them on one stream or synchronise between them.  The status word is
+ * cleared by each call; a timed-out staging wait leaves Y incomplete and is
+ * not reported by this entry point.  Asynchronous on `stream`.
+ * Errors: SPMM_ERR_ARG (sizes, NULL, more than 16384 segments),
+ * SPMM_ERR_UNSUPPORTED (value/X type mix), SPMM_ERR_CUDA.
+ */
+int spmm_apply_csr_static(int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t* row_ptr,
+                          const int32_t* col_idx, const void* values, spmm_dtype vtype, const int32_t* tasks,
+                          int64_t n_tasks, int64_t n_segments, const void* X, int64_t ldx, int32_t k,
+                          spmm_dtype xtype, float* Y, int64_t ldy, void* stream);
+
 /* spmm_get_info -- plan statistics of a handle (host call, no GPU work). */
 int spmm_get_info(spmm_mat_t A, spmm_info* info);
 

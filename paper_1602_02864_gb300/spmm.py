@@ -68,6 +68,9 @@ _lib.spmm_debug_wait_timeout.restype = ctypes.c_int
 _lib.spmm_plan_tasks.argtypes = [_i64, _P, ctypes.POINTER(spmm_opts), _P, ctypes.POINTER(_i64),
                                  ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
 _lib.spmm_plan_tasks.restype = ctypes.c_int
+_lib.spmm_apply_csr_static.argtypes = [_i64, _i64, _i64, _P, _P, _P, ctypes.c_int, _P, _i64, _i64, _P, _i64,
+                                       _i32, ctypes.c_int, _P, _i64, _P]
+_lib.spmm_apply_csr_static.restype = ctypes.c_int
 _lib.spmm_last_error.argtypes = []
 _lib.spmm_last_error.restype = ctypes.c_char_p
 
@@ -171,6 +174,14 @@ def spmm_plan_tasks(row_ptr, opts: spmm_opts | None = None):
     _check(_lib.spmm_plan_tasks(n_rows, _ptr(rp), o, _ptr(tasks), ctypes.byref(nt), ctypes.byref(ns),
                                 ctypes.byref(nseg)))
     return tasks, ns.value, nseg.value
+
+
+def spmm_apply_csr_static(n_rows, n_cols, nnz, row_ptr, col_idx, values, vtype, tasks, n_tasks, n_segments, X,
+                          ldx, k, xtype, Y, ldy, stream=None):
+    """Allocation-free Y = A X on caller-owned device buffers (see spmm.h)."""
+    _check(_lib.spmm_apply_csr_static(int(n_rows), int(n_cols), int(nnz), _ptr(row_ptr), _ptr(col_idx),
+                                      _ptr(values), int(vtype), _ptr(tasks), int(n_tasks), int(n_segments), _ptr(X),
+                                      int(ldx), int(k), int(xtype), _ptr(Y), int(ldy), _stream_handle(stream)))
 
 
 def spmm_get_info(h) -> dict:

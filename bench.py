@@ -1,10 +1,11 @@
 """SpMM benchmark: in-HBM Y = A X on an R-MAT scale-24 power-law graph.
 
 Workload (one step): Y = A X for every k in the sweep {1, 2, 4, 8, 16, 32, 64}
-with float32 X, A the pattern-only adjacency matrix of a seeded R-MAT graph
-(2^24 vertices, 2^28 generated directed edges, a/b/c/d = .57/.19/.19/.05,
-duplicates merged).  The headline value is nonzeros processed per second over
-the whole step (sum over k of nnz / step time).  Per k the line also reports
+with float32 X, then 30 PageRank iterations (damping 0.85, one CUDA graph, one
+A^T product per iteration), A the pattern-only adjacency matrix of a seeded
+R-MAT graph (2^24 vertices, 2^28 generated directed edges, a/b/c/d =
+.57/.19/.19/.05, duplicates merged).  The headline value is nonzeros processed
+per second over the whole step ((7 + 30) * nnz / step time).  Per k the line also reports
 nnz/s, the algorithmic bytes moved per call
     nnz*(4 + value bytes) + 8*(N+1) + N*k*(X element bytes) + N*k*4
 as GB/s and as a fraction of the measured HBM copy bandwidth, and the BF16-X
@@ -51,11 +52,20 @@ def parse():
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--pagerank-iters", type=int, default=30)
     return ap.parse_args()
 
 
 def metric_name(args):
-    return f"SpMM nonzeros/s (R-MAT scale {args.scale}, k sweep {args.ks}, FP32 X)"
+    pr = f" + PageRank x{args.pagerank_iters}" if args.pagerank_iters else ""
+    return f"SpMM nonzeros/s (R-MAT scale {args.scale}, k sweep {args.ks}{pr}, FP32 X)"
+
+
+def pagerank_iter_bytes(nnz, n):
+    """Algorithmic bytes of one PageRank iteration: the A^T product at k = 1
+    (column indices, row pointers, z in, y out) plus the update (y, x read and
+    written, out-degree, z written)."""
+    return alg_bytes(nnz, n, n, 1, 4) + 5 * 4 * n
 
 
 def alg_bytes(nnz, n_rows, n_cols, k, xbytes, vbytes=0):
@@ -143,11 +153,13 @@ def cpu_sample_rows(A, target_nnz, seed=7):
     return rows, nz
 
 
-def run_cpu_oracle(A, Xh, ks, rows, threads):
+def run_cpu_oracle(A, Xh, ks, rows, threads, pr_iters=0):
     import oracle
     t = time.perf_counter()
     for k in ks:
         oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xh, rows, threads=threads, k=k)
+    if pr_iters:
+        oracle.pagerank(A.n_rows, A.row_ptr, A.col_idx, 0.85, pr_iters)
     return time.perf_counter() - t
 
 
@@ -167,11 +179,12 @@ def reference_arm(args, rank, world):
     rate = nz * len(ks) / dt
     target = rate * max(args.cpu_seconds / 4, 0.5) / len(ks)
     rows, nz = cpu_sample_rows(A, target, seed=8)
+    pr = 1 if args.pagerank_iters else 0
     for _ in range(args.warmup):
         run_cpu_oracle(A, Xh, ks, rows[: max(1, len(rows) // 8)], threads)
-    times = [run_cpu_oracle(A, Xh, ks, rows, threads) for _ in range(args.steps)]
+    times = [run_cpu_oracle(A, Xh, ks, rows, threads, pr) for _ in range(args.steps)]
     total = sum(times)
-    value = nz * len(ks) * args.steps / total
+    value = (nz * len(ks) + pr * A.nnz) * args.steps / total
     line = {
         "impl": "reference", "metric": metric_name(args), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
@@ -180,7 +193,7 @@ def reference_arm(args, rank, world):
                    "nnz": A.nnz, "ks": ks},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{len(rows)} seeded rows ({nz} nonzeros) of the scale-{args.scale} graph, "
-                                   f"all k in the sweep, per step"},
+                                   f"all k in the sweep, plus {pr} full PageRank iteration, per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -212,7 +225,7 @@ def main():
     A, t_gen = make_graph(args)
     N, nnz = A.n_rows, A.nnz
     t0 = time.time()
-    h = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None)
+    h = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, transpose=args.pagerank_iters > 0)
     torch.cuda.synchronize()
     t_create = time.time() - t0
     info = h.info()
@@ -224,6 +237,9 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     launches_per_apply = 1 + (1 if info["n_split_rows"] > 0 else 0)
+    launches_per_pr_iter = 3 + (1 if info["n_split_rows_t"] > 0 else 0)
+    xpr = torch.empty(N, dtype=torch.float32, device=dev)
+    pr_res = [None]
 
     def step(xs, ev=None):
         for i, k in enumerate(ks):
@@ -232,6 +248,12 @@ def main():
             h.apply(xs[k], Y=Y[k])
             if ev is not None:
                 ev[i][1].record(stream)
+        if args.pagerank_iters:
+            if ev is not None:
+                ev[-1][0].record(stream)
+            _, pr_res[0] = h.pagerank(0.85, args.pagerank_iters, x=xpr)
+            if ev is not None:
+                ev[-1][1].record(stream)
 
     # ---- warm-up, then the timed steps (L2 flushed before every step)
     for _ in range(args.warmup):
@@ -239,18 +261,23 @@ def main():
         step(X)
     barrier()
     per_k = {k: [] for k in ks}
+    pr_ms = []
     step_ms = []
     peak_gbs, peak_kind = load_peaks()
     with ClockSampler(local) as clk:
         barrier()
         for _ in range(args.steps):
             flush.zero_()
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in ks]
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(len(ks) + 1)]
             step(X, ev)
             torch.cuda.synchronize()
             ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(len(ks))]
             for i, k in enumerate(ks):
                 per_k[k].append(ms[i])
+            if args.pagerank_iters:
+                pr_ms.append(ev[-1][0].elapsed_time(ev[-1][1]))
+                ms.append(pr_ms[-1])
             step_ms.append(sum(ms))
         barrier()
     t_total = sum(step_ms) / 1e3
@@ -258,7 +285,7 @@ def main():
         tt = torch.tensor([t_total], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_total = float(tt.item())
-    value = world * nnz * len(ks) * args.steps / t_total
+    value = world * nnz * (len(ks) + args.pagerank_iters) * args.steps / t_total
 
     # ---- per-k breakdown; roofline of the dominant launch
     breakdown = {}
@@ -269,6 +296,21 @@ def main():
                              "roofline_frac": B / (ms / 1e3) / 1e9 / peak_gbs}
     kdom = max(ks, key=lambda k: statistics.mean(per_k[k]))
     dom = breakdown[str(kdom)]
+    dom_name = f"rows_kernel k={kdom} f32"
+    pagerank = None
+    if args.pagerank_iters:
+        ms = statistics.mean(pr_ms)
+        it_ms = ms / args.pagerank_iters
+        B = pagerank_iter_bytes(nnz, N)
+        xh = xpr.double().cpu().numpy()
+        pagerank = {"iters": args.pagerank_iters, "ms": round(ms, 3), "ms_per_iter": round(it_ms, 4),
+                    "nnz_per_s": nnz / (it_ms / 1e3), "alg_GBps": B / (it_ms / 1e3) / 1e9,
+                    "roofline_frac": B / (it_ms / 1e3) / 1e9 / peak_gbs, "sum_x": float(xh.sum()),
+                    "min_x": float(xh.min()), "residual_first_last": [float(pr_res[0][0]), float(pr_res[0][-1])]}
+        if ms > statistics.mean(per_k[kdom]):
+            dom = pagerank
+            dom_name = ("PageRank iteration: rows_kernel on A^T (k=1, f32) + update + reduce; "
+                        f"{args.pagerank_iters} per CUDA-graph launch, timed per call")
 
     # ---- BF16 X: speedup over FP32 and error on sampled rows vs the oracle
     import oracle
@@ -327,18 +369,23 @@ def main():
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = max(1, min(args.steps, 5))
+        xp_host = torch.empty(N, dtype=torch.float32).pin_memory()
         e0.record(stream)
         for _ in range(reps):
             for k in ks:
                 Xd[k].copy_(Xp[k], non_blocking=True)
                 h.apply(Xd[k], Y=Y[k])
                 Yp[k].copy_(Y[k], non_blocking=True)
+            if args.pagerank_iters:
+                h.pagerank(0.85, args.pagerank_iters, x=xpr)
+                xp_host.copy_(xpr, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
         te = e0.elapsed_time(e1) / 1e3
         hb = sum(N * k * 4 for k in ks)
-        e2e = {"value": world * nnz * len(ks) * reps / te, "unit": UNIT, "h2d_bytes_per_step": hb,
-               "d2h_bytes_per_step": hb}
+        db = hb + (N * 4 if args.pagerank_iters else 0)
+        e2e = {"value": world * nnz * (len(ks) + args.pagerank_iters) * reps / te, "unit": UNIT,
+               "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
         del Xp, Yp, Xd
 
     # ---- CPU baseline: the oracle on a bounded row sample, all host cores
@@ -349,10 +396,11 @@ def main():
         dt = run_cpu_oracle(A, Xh, ks, rows, threads)
         target = nz * args.cpu_seconds / max(dt, 1e-3) / 2
         rows, nz = cpu_sample_rows(A, target, seed=9)
-        dt = run_cpu_oracle(A, Xh, ks, rows, threads)
-        cpu = {"value": nz * len(ks) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{len(rows)} seeded rows ({nz} nonzeros) of the scale-{args.scale} graph, "
-                         f"FP64, every k in the sweep ({dt:.1f} s)"}
+        pr = 1 if args.pagerank_iters else 0
+        dt = run_cpu_oracle(A, Xh, ks, rows, threads, pr)
+        cpu = {"value": (nz * len(ks) + pr * nnz) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{len(rows)} seeded rows ({nz} nonzeros) of the scale-{args.scale} graph, FP64, "
+                         f"every k in the sweep, plus {pr} full PageRank iteration (serial) ({dt:.1f} s)"}
 
     if rank == 0:
         line = {
@@ -367,12 +415,14 @@ def main():
             "bf16": bf16,
             "parity_max_err_over_absprod": parity,
             "roofline": {"bound": "hbm", "achieved": dom["alg_GBps"], "peak": peak_gbs, "unit": "GB/s",
-                         "frac": dom["roofline_frac"], "traffic": None, "kernel": f"rows_kernel k={kdom} f32",
+                         "frac": dom["roofline_frac"], "traffic": None, "kernel": dom_name,
                          "peak_kind": peak_kind},
+            "pagerank": pagerank,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
-            "gpu_launches": launches_per_apply * len(ks) * args.steps,
+            "gpu_launches": (launches_per_apply * len(ks) + launches_per_pr_iter * args.pagerank_iters
+                             + (4 if args.pagerank_iters else 0)) * args.steps,
             "setup_s": {"generate": round(t_gen, 2), "create": round(t_create, 2)},
             "plan": {"tasks": info["n_tasks"], "split_rows": info["n_split_rows"], "segments": info["n_segments"]},
         }

@@ -206,6 +206,27 @@ int spmm_apply_csr_static(int64_t n_rows, int64_t n_cols, int64_t nnz, const int
                           int64_t n_tasks, int64_t n_segments, const void* X, int64_t ldx, int32_t k,
                           spmm_dtype xtype, float* Y, int64_t ldy, void* stream);
 
+/*
+ * spmm_pagerank -- PageRank by power iteration (Section 4.1):
+ *   x'(u) = (1-d)/N + d * sum_{v in B(u)} x(v)/L(v) + d * (sum_{L(v)=0} x(v)) / N
+ * B(u) = in-neighbours of u, L(v) = out-degree of v; row v of A lists the
+ * out-links of v; the rank of dangling vertices (L = 0) is spread uniformly.
+ * Each iteration is one A^T product (k = 1, float32) plus a fused update with
+ * FP64 reductions; all iterations run as one CUDA graph.
+ *   A          square pattern handle (created without values) with SPMM_WANT_TRANSPOSE
+ *   damping    d in [0, 1]
+ *   iters      number of iterations (>= 0, no early stop)
+ *   x          device float[N]: the ranks after `iters` iterations
+ *   x0         device float[N] start vector, or NULL for 1/N
+ *   residuals  host double[iters] or NULL: sum_u |x'(u) - x(u)| of each iteration (FP64)
+ * Synchronises `stream` first, then runs on an internal stream and returns
+ * when the ranks are ready.  Allocates and frees its workspace (4 floats per
+ * vertex).  Errors: SPMM_ERR_ARG (NULL, non-square, values present, no
+ * transpose, bad d or iters), SPMM_ERR_TIMEOUT, SPMM_ERR_OOM, SPMM_ERR_CUDA.
+ */
+int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float* x, const float* x0, double* residuals,
+                  void* stream);
+
 /* spmm_get_info -- plan statistics of a handle (host call, no GPU work). */
 int spmm_get_info(spmm_mat_t A, spmm_info* info);
 

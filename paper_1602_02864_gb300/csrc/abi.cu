@@ -22,7 +22,7 @@ constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every device-side stag
 
 void set_error(const std::string& msg) { g_error = msg; }
 
-static int cuda_fail(cudaError_t e, const char* what) {
+int cuda_fail(cudaError_t e, const char* what) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? SPMM_ERR_OOM : SPMM_ERR_CUDA;
 }
@@ -232,23 +232,14 @@ extern "C" int spmm_create_csr(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, 
     return SPMM_OK;
 }
 
-extern "C" int spmm_apply(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype xtype, void* Y,
-                          int64_t ldy, spmm_dtype ytype, int32_t transpose, void* stream) {
-    if (!A) { set_error("spmm_apply: A is NULL"); return SPMM_ERR_ARG; }
-    if (k < 1 || k > kMaxK) { set_error("spmm_apply: k must be in 1..64"); return SPMM_ERR_ARG; }
-    if (ldx < k || ldy < k) { set_error("spmm_apply: ldx and ldy must be >= k"); return SPMM_ERR_ARG; }
-    if (ytype != SPMM_F32) { set_error("spmm_apply: Y must be F32"); return SPMM_ERR_ARG; }
-    if (xtype != SPMM_F32 && xtype != SPMM_BF16 && xtype != SPMM_F16) {
-        set_error("spmm_apply: X must be F32, BF16 or F16");
-        return SPMM_ERR_ARG;
-    }
-    if (transpose && !A->has_tr) {
-        set_error("spmm_apply: transpose needs SPMM_WANT_TRANSPOSE at create");
-        return SPMM_ERR_ARG;
-    }
+namespace spmm {
+
+// Enqueue Y = A X (or A^T X) for a validated handle; shared by spmm_apply and
+// the applications built on it.
+int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
+              int64_t ldy, cudaStream_t s) {
     const DevCSR& d = transpose ? A->tr : A->fwd;
     if (d.n_rows == 0) return SPMM_OK;
-    if (!X || !Y) { set_error("spmm_apply: X or Y is NULL"); return SPMM_ERR_ARG; }
     int vmode = 0;
     if (A->vtype == SPMM_F32) vmode = 1;
     else if (A->vtype == SPMM_BF16) vmode = 2;
@@ -285,20 +276,41 @@ extern "C" int spmm_apply(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, s
     a.x_evict_last = A->params.x_evict_last;
     a.X = X;
     a.ldx = ldx;
-    a.Y = (float*)Y;
+    a.Y = Y;
     a.ldy = ldy;
     a.k = k;
     a.lanes_log2 = lg;
     a.nvec = nvec;
-    cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     if (xtype == SPMM_F32) e = launch_rows_f32(a, vmode, vec, ch, s);
     else if (xtype == SPMM_BF16) e = launch_rows_bf16(a, vmode, vec, ch, s);
     else e = launch_rows_f16(a, vmode, vec, ch, s);
-    if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: row-task kernel");
-    e = launch_combine(d.splits, d.n_splits, d.partials, (float*)Y, ldy, k, s);
+    if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: task kernel");
+    e = launch_combine(d.splits, d.n_splits, d.partials, Y, ldy, k, s);
     if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: combine kernel");
     return SPMM_OK;
+}
+
+}  // namespace spmm
+
+extern "C" int spmm_apply(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype xtype, void* Y,
+                          int64_t ldy, spmm_dtype ytype, int32_t transpose, void* stream) {
+    if (!A) { set_error("spmm_apply: A is NULL"); return SPMM_ERR_ARG; }
+    if (k < 1 || k > kMaxK) { set_error("spmm_apply: k must be in 1..64"); return SPMM_ERR_ARG; }
+    if (ldx < k || ldy < k) { set_error("spmm_apply: ldx and ldy must be >= k"); return SPMM_ERR_ARG; }
+    if (ytype != SPMM_F32) { set_error("spmm_apply: Y must be F32"); return SPMM_ERR_ARG; }
+    if (xtype != SPMM_F32 && xtype != SPMM_BF16 && xtype != SPMM_F16) {
+        set_error("spmm_apply: X must be F32, BF16 or F16");
+        return SPMM_ERR_ARG;
+    }
+    if (transpose && !A->has_tr) {
+        set_error("spmm_apply: transpose needs SPMM_WANT_TRANSPOSE at create");
+        return SPMM_ERR_ARG;
+    }
+    const DevCSR& d = transpose ? A->tr : A->fwd;
+    if (d.n_rows == 0) return SPMM_OK;
+    if (!X || !Y) { set_error("spmm_apply: X or Y is NULL"); return SPMM_ERR_ARG; }
+    return apply_dev(A, transpose, X, ldx, k, (int32_t)xtype, (float*)Y, ldy, (cudaStream_t)stream);
 }
 
 extern "C" int spmm_get_info(spmm_mat_t A, spmm_info* info) {

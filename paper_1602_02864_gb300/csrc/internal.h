@@ -81,6 +81,9 @@ HostPlan build_plan(const int64_t* row_ptr, int64_t n_rows, const Params& p);
 
 // abi.cu
 void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
+              int64_t ldy, cudaStream_t s);
 
 // Arguments of the task kernel (one instantiation per x type / value type /
 // vector width / column chunks).

@@ -1,0 +1,208 @@
+// pagerank.cu -- PageRank power iteration on the SpMM path (paper Section 4.1).
+//
+// Update rule (Section 4.1): PR(u) = (1-d)/N + d * sum_{v in B(u)} PR(v)/L(v),
+// with B(u) the in-neighbours of u and L(v) the out-degree of v; the rank of
+// dangling vertices (L = 0) is spread uniformly, so the ranks keep summing to 1.
+// Row v of A lists the out-links of v, so the in-neighbour sum is the product
+// with the transposed matrix: y = A^T z with z[v] = x[v] / L(v).
+//
+// One iteration = the task kernel on A^T (k = 1, float32) + one fused
+// elementwise kernel (new ranks, the next z, FP64 per-block partial sums of the
+// L1 change and of the dangling mass) + a one-block kernel adding the partials
+// in a fixed order.  All iterations are captured into one CUDA graph and
+// launched once.  Ranks are float32; every reduction is FP64 and run-to-run
+// deterministic.
+#include <vector>
+
+#include "internal.h"
+
+namespace spmm {
+
+constexpr int kPrThreads = 256;
+
+// Fixed-order block sum of a double (xor tree inside warps, then warp sums
+// added in warp order by thread 0).  Result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    __syncthreads();
+    return s;
+}
+
+// outdeg[v] = L(v) as float (0 for dangling vertices); x = x0 or 1/N.
+__global__ void pr_init_kernel(const int64_t* __restrict__ row_ptr, int64_t n, float* __restrict__ outdeg,
+                               float* __restrict__ x, const float* __restrict__ x0) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        outdeg[i] = (float)(row_ptr[i + 1] - row_ptr[i]);
+        x[i] = x0 ? x0[i] : (float)(1.0 / (double)n);
+    }
+}
+
+// z = x / L (0 where L = 0); per-block partial of the dangling mass.
+__global__ void pr_scale_kernel(const float* __restrict__ x, const float* __restrict__ outdeg, int64_t n,
+                                float* __restrict__ z, double* __restrict__ part_dang) {
+    __shared__ double sh[32];
+    double dang = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float L = outdeg[i], xi = x[i];
+        if (L > 0.f) z[i] = xi / L;
+        else { z[i] = 0.f; dang += (double)xi; }
+    }
+    const double s = block_sum(dang, sh);
+    if (threadIdx.x == 0) part_dang[blockIdx.x] = s;
+}
+
+// x' = (1-d)/N + d*D/N + d*y, with D the dangling mass of x (scal[0]);
+// partials of sum |x' - x| and of the dangling mass of x'; z' = x' / L.
+__global__ void pr_update_kernel(const float* __restrict__ y, float* __restrict__ x, const float* __restrict__ outdeg,
+                                 int64_t n, double d, const double* __restrict__ scal, float* __restrict__ z,
+                                 double* __restrict__ part_res, double* __restrict__ part_dang) {
+    __shared__ double sh[32];
+    const double base = (1.0 - d) / (double)n + d * scal[0] / (double)n;
+    double res = 0.0, dang = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float xn = (float)(base + d * (double)y[i]);
+        res += fabs((double)xn - (double)x[i]);
+        x[i] = xn;
+        const float L = outdeg[i];
+        if (L > 0.f) z[i] = xn / L;
+        else { z[i] = 0.f; dang += (double)xn; }
+    }
+    const double s1 = block_sum(res, sh);
+    const double s2 = block_sum(dang, sh);
+    if (threadIdx.x == 0) {
+        part_res[blockIdx.x] = s1;
+        part_dang[blockIdx.x] = s2;
+    }
+}
+
+// scal[0] = sum of the dangling partials; res_out (if given) = sum of the
+// residual partials; both in block order.
+__global__ void pr_reduce_kernel(const double* __restrict__ part_dang, const double* __restrict__ part_res,
+                                 int nparts, double* __restrict__ scal, double* __restrict__ res_out) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        a += part_dang[i];
+        if (res_out) b += part_res[i];
+    }
+    const double sa = block_sum(a, sh);
+    const double sb = block_sum(b, sh);
+    if (threadIdx.x == 0) {
+        scal[0] = sa;
+        if (res_out) *res_out = sb;
+    }
+}
+
+}  // namespace spmm
+
+using namespace spmm;
+
+extern "C" int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float* x, const float* x0,
+                             double* residuals, void* stream) {
+    if (!A || !x) { set_error("spmm_pagerank: NULL argument"); return SPMM_ERR_ARG; }
+    if (A->fwd.n_rows != A->fwd.n_cols || A->fwd.n_rows < 1) {
+        set_error("spmm_pagerank: the matrix must be square and non-empty");
+        return SPMM_ERR_ARG;
+    }
+    if (!A->has_tr) { set_error("spmm_pagerank: needs SPMM_WANT_TRANSPOSE at create"); return SPMM_ERR_ARG; }
+    if (A->vtype != -1) {
+        set_error("spmm_pagerank: PageRank walks the graph pattern; create the handle without values");
+        return SPMM_ERR_ARG;
+    }
+    if (iters < 0 || !(damping >= 0.0 && damping <= 1.0)) {
+        set_error("spmm_pagerank: need iters >= 0 and 0 <= damping <= 1");
+        return SPMM_ERR_ARG;
+    }
+    const int64_t n = A->fwd.n_rows;
+    cudaStream_t user = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "spmm_pagerank: device query");
+    const int nblk = sms * 8;
+    // workspace: outdeg, z, y (float n each), partials (2 x nblk), scalar, residuals
+    float *outdeg = nullptr, *z = nullptr, *y = nullptr;
+    double *part = nullptr, *scal = nullptr, *dres = nullptr;
+    cudaStream_t s = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = SPMM_OK;
+    auto fail = [&](cudaError_t err, const char* what) { rc = cuda_fail(err, what); };
+    do {
+        if ((e = cudaStreamSynchronize(user)) != cudaSuccess) { fail(e, "spmm_pagerank: stream"); break; }
+        if ((e = cudaMalloc((void**)&outdeg, n * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&z, n * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&y, n * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&part, 2 * (size_t)nblk * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&scal, 8 * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&dres, (size_t)(iters > 0 ? iters : 1) * sizeof(double))) != cudaSuccess) {
+            fail(e, "spmm_pagerank: workspace");
+            break;
+        }
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) {
+            fail(e, "spmm_pagerank: stream create");
+            break;
+        }
+        // set-up outside the graph
+        pr_init_kernel<<<nblk, kPrThreads, 0, s>>>(A->fwd.row_ptr, n, outdeg, x, x0);
+        pr_scale_kernel<<<nblk, kPrThreads, 0, s>>>(x, outdeg, n, z, part);
+        pr_reduce_kernel<<<1, kPrThreads, 0, s>>>(part, nullptr, nblk, scal, nullptr);
+        if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "spmm_pagerank: init"); break; }
+        // warm the task kernel's launch configuration outside the capture
+        if ((rc = apply_dev(A, 1, z, 1, 1, SPMM_F32, y, 1, s)) != SPMM_OK) break;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "spmm_pagerank: init sync"); break; }
+        if (iters > 0) {
+            if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+                fail(e, "spmm_pagerank: capture");
+                break;
+            }
+            for (int32_t t = 0; t < iters && rc == SPMM_OK; ++t) {
+                rc = apply_dev(A, 1, z, 1, 1, SPMM_F32, y, 1, s);
+                if (rc != SPMM_OK) break;
+                pr_update_kernel<<<nblk, kPrThreads, 0, s>>>(y, x, outdeg, n, damping, scal, z, part + nblk, part);
+                pr_reduce_kernel<<<1, kPrThreads, 0, s>>>(part, part + nblk, nblk, scal, dres + t);
+            }
+            cudaError_t ec = cudaStreamEndCapture(s, &graph);
+            if (rc != SPMM_OK) break;
+            if (ec != cudaSuccess) { fail(ec, "spmm_pagerank: end capture"); break; }
+            if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) { fail(e, "spmm_pagerank: instantiate"); break; }
+            if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) { fail(e, "spmm_pagerank: launch"); break; }
+        }
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "spmm_pagerank: run"); break; }
+        int32_t st = 0;
+        if ((e = cudaMemcpy(&st, A->status, sizeof(st), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            fail(e, "spmm_pagerank: status");
+            break;
+        }
+        if (st != 0) {
+            cudaMemset(A->status, 0, sizeof(int32_t));
+            set_error("spmm_pagerank: a device-side staging wait timed out; the ranks are incomplete");
+            rc = SPMM_ERR_TIMEOUT;
+            break;
+        }
+        if (residuals && iters > 0 &&
+            (e = cudaMemcpy(residuals, dres, (size_t)iters * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            fail(e, "spmm_pagerank: residuals");
+            break;
+        }
+    } while (0);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(outdeg);
+    cudaFree(z);
+    cudaFree(y);
+    cudaFree(part);
+    cudaFree(scal);
+    cudaFree(dres);
+    return rc;
+}

@@ -71,6 +71,8 @@ _lib.spmm_plan_tasks.restype = ctypes.c_int
 _lib.spmm_apply_csr_static.argtypes = [_i64, _i64, _i64, _P, _P, _P, ctypes.c_int, _P, _i64, _i64, _P, _i64,
                                        _i32, ctypes.c_int, _P, _i64, _P]
 _lib.spmm_apply_csr_static.restype = ctypes.c_int
+_lib.spmm_pagerank.argtypes = [_P, ctypes.c_double, _i32, _P, _P, _P, _P]
+_lib.spmm_pagerank.restype = ctypes.c_int
 _lib.spmm_last_error.argtypes = []
 _lib.spmm_last_error.restype = ctypes.c_char_p
 
@@ -184,6 +186,14 @@ def spmm_apply_csr_static(n_rows, n_cols, nnz, row_ptr, col_idx, values, vtype, 
                                       int(ldx), int(k), int(xtype), _ptr(Y), int(ldy), _stream_handle(stream)))
 
 
+def spmm_pagerank(h, damping, iters, x, x0=None, stream=None) -> np.ndarray:
+    """PageRank into the float32 CUDA tensor x; returns the FP64 residuals."""
+    res = np.zeros(max(int(iters), 1), dtype=np.float64)
+    _check(_lib.spmm_pagerank(h, float(damping), int(iters), _ptr(x), _ptr(x0), _P(res.ctypes.data),
+                              _stream_handle(stream)))
+    return res[:int(iters)]
+
+
 def spmm_get_info(h) -> dict:
     info = spmm_info()
     _check(_lib.spmm_get_info(h, ctypes.byref(info)))
@@ -228,6 +238,14 @@ class SparseMatrix:
 
     def sync_status(self, stream=None):
         spmm_sync_status(self.handle, stream)
+
+    def pagerank(self, damping=0.85, iters=30, x0=None, x=None, stream=None):
+        """Returns (x, residuals) -- x a float32 CUDA tensor of the ranks."""
+        import torch
+        if x is None:
+            x = torch.empty(self.n_rows, dtype=torch.float32, device="cuda")
+        res = spmm_pagerank(self.handle, damping, iters, x, x0, stream)
+        return x, res
 
     def close(self):
         if self.handle is not None and self.handle.value:

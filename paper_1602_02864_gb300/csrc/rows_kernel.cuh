@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
     // nonzeros in flight per lane group
     constexpr int kBytes = VEC * CH * (int)sizeof(XT);
     constexpr int kU = SPMM_UNROLL_BYTES / kBytes;
-    constexpr int U = kU < 2 ? 2 : (kU > 16 ? 16 : kU);
+    constexpr int U = kU < 2 ? 2 : (kU > 8 ? 8 : kU);
     extern __shared__ __align__(128) unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* wb = smem + w * Lay::kWarp;
@@ -357,7 +357,42 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
             }
             st.rp = reinterpret_cast<const int64_t*>(buf + Lay::kRpOff) + (d0.x & 1);
 
-            if (d0.y > 0) {
+            if (VEC == 1 && CH == 1 && lg == 0 && d0.y > 0) {
+                // k = 1, run of short rows: every lane gathers the task's
+                // nonzeros as one flat array (lane, lane+32, ...) and writes each
+                // product over its staged column index; then lane j adds the
+                // products of rows j, j+32 in nonzero order from shared memory.
+                const int nr = d0.y;
+                int32_t* prod = const_cast<int32_t*>(st.col);
+                constexpr int UF = 8;
+                for (int base = 0; base < n; base += 32 * UF) {
+                    float xv[UF], av[UF];
+#pragma unroll
+                    for (int u = 0; u < UF; ++u) {
+                        const int idx = base + lane + 32 * u;
+                        if (idx < n) {
+                            const int64_t cidx = st.col[idx];
+                            av[u] = staged_val<VMODE>(st.val, idx);
+                            XVec<XT, 1> t1;
+                            t1.load(xb + cidx * a.ldx, xpol);
+                            xv[u] = t1.get(0);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < UF; ++u) {
+                        const int idx = base + lane + 32 * u;
+                        if (idx < n) prod[idx] = __float_as_int(av[u] * xv[u]);
+                    }
+                }
+                __syncwarp();
+                for (int j = lane; j < nr; j += 32) {
+                    const int s = (int)(st.rp[j] - e0), e = (int)(st.rp[j + 1] - e0);
+                    float acc = 0.f;
+                    for (int i = s; i < e; ++i) acc += __int_as_float(prod[i]);
+                    __stcs(a.Y + (int64_t)(d0.x + j) * a.ldy, acc);
+                }
+                fence_proxy_async();   // the products were written where the next copy lands
+            } else if (d0.y > 0) {
                 // run of short rows: lane group g owns rows g, g+G, ...
                 const int nr = d0.y;
                 for (int j = g; j < nr; j += G) {

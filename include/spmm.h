@@ -88,6 +88,8 @@ typedef struct {
     int64_t device_bytes;        /* device memory held by the handle                */
     int32_t value_dtype;         /* spmm_dtype of the stored values, -1 = pattern   */
     int32_t has_transpose;
+    int32_t n_graphs;            /* graphs in a batched handle (1 otherwise)        */
+    int32_t reserved;
 } spmm_info;
 
 /*
@@ -112,6 +114,26 @@ typedef struct {
 int spmm_create_csr(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, int64_t nnz,
                     const int64_t* row_ptr, const int32_t* col_idx, const void* values,
                     spmm_dtype vtype, uint32_t flags, const spmm_opts* opts, void* stream);
+
+/*
+ * spmm_create_batched -- one handle for a batch of independent graphs, stored
+ * as one block-diagonal matrix: graph g owns the row block and the column
+ * block that follow the blocks of graphs 0..g-1.  One spmm_apply on the
+ * handle then runs every graph's warp tasks in a single persistent launch
+ * (the GPU form of keeping many small multiplications busy at once); X and Y
+ * are the graphs' dense matrices stacked in graph order (row offsets = the
+ * running sums of n_cols for X and n_rows for Y, or the reverse for A^T X).
+ *   n_graphs     number of graphs (>= 1)
+ *   n_rows[g], n_cols[g]   shape of graph g
+ *   row_ptrs[g], col_idxs[g]   host CSR of graph g (local column indices)
+ *   values       NULL (pattern) or an array of n_graphs host value arrays of vtype
+ *   flags, opts, stream    as for spmm_create_csr
+ * Totals must stay below 2^31 rows and columns.  Errors as spmm_create_csr.
+ */
+int spmm_create_batched(spmm_mat_t* out, int32_t n_graphs, const int64_t* n_rows, const int64_t* n_cols,
+                        const int64_t* const* row_ptrs, const int32_t* const* col_idxs,
+                        const void* const* values, spmm_dtype vtype, uint32_t flags, const spmm_opts* opts,
+                        void* stream);
 
 /*
  * spmm_apply -- Y = A X (transpose = 0) or Y = A^T X (transpose = 1)
@@ -226,6 +248,34 @@ int spmm_apply_csr_static(int64_t n_rows, int64_t n_cols, int64_t nnz, const int
  */
 int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float* x, const float* x0, double* residuals,
                   void* stream);
+
+/*
+ * spmm_nmf -- non-negative matrix factorisation A ~ W H by the multiplicative
+ * updates of Section 4.3, H first, then W, for `steps` steps:
+ *   Ht <- Ht o (A^T W) / (Ht (W^T W) + eps),   W <- W o (A Ht) / (W (Ht^T Ht) + eps)
+ * H is stored transposed (Ht).  Each step is two SpMMs (A Ht and A^T W) plus
+ * two k x k Gram matrices and two row-local updates; all steps run as one CUDA
+ * graph.  On a batched handle every graph is factorised independently (its own
+ * Grams and objective) while the SpMMs cover the whole batch in one launch.
+ *   A          handle created with SPMM_WANT_TRANSPOSE (single or batched)
+ *   k          rank, 1..64
+ *   steps      number of H-then-W steps (>= 0)
+ *   W          device float32, row-major (total rows) x k, contiguous (ld = k);
+ *              in: initial factor (non-negative), out: factor after `steps`
+ *   Ht         device float32, (total columns) x k, contiguous; in/out likewise
+ *   ftype      SPMM_F32: the SpMMs read the float32 factors; SPMM_BF16: they read
+ *              a bfloat16 copy (float32 accumulation); updates stay float32
+ *   eps        added to every denominator (1e-12 keeps 0/0 at 0)
+ *   objective  host double[n_graphs * (steps+1)] or NULL: for graph g,
+ *              objective[g*(steps+1) + t] = ||A_g - W_g H_g||_F^2 before step t
+ *              (t = steps: after the last), from ||A||^2 - 2 sum(W o A Ht)
+ *              + tr((W^T W)(Ht^T Ht)) in FP64
+ * Synchronises `stream`, runs on an internal stream, allocates its workspace.
+ * Errors: SPMM_ERR_ARG, SPMM_ERR_UNSUPPORTED (16-bit values with the other
+ * factor type), SPMM_ERR_TIMEOUT, SPMM_ERR_OOM, SPMM_ERR_CUDA.
+ */
+int spmm_nmf(spmm_mat_t A, int32_t k, int32_t steps, float* W, float* Ht, spmm_dtype ftype, double eps,
+             double* objective, void* stream);
 
 /* spmm_get_info -- plan statistics of a handle (host call, no GPU work). */
 int spmm_get_info(spmm_mat_t A, spmm_info* info);

@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "internal.h"
 
 namespace spmm {
@@ -147,51 +149,78 @@ extern "C" int spmm_plan_tasks(int64_t n_rows, const int64_t* row_ptr, const spm
 
 extern "C" const char* spmm_last_error(void) { return g_error.c_str(); }
 
-extern "C" int spmm_create_csr(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, int64_t nnz,
-                               const int64_t* row_ptr, const int32_t* col_idx, const void* values,
-                               spmm_dtype vtype, uint32_t flags, const spmm_opts* opts, void* stream) {
-    set_error("");
-    if (!out) { set_error("spmm_create_csr: out is NULL"); return SPMM_ERR_ARG; }
+namespace spmm {
+
+// Host value of stored entry p (for ||A||^2 of each graph).
+static double host_value(const void* v, int32_t vtype, int64_t p) {
+    if (!v) return 1.0;
+    if (vtype == SPMM_F32) return (double)static_cast<const float*>(v)[p];
+    const uint16_t b = static_cast<const uint16_t*>(v)[p];
+    if (vtype == SPMM_BF16) {
+        const uint32_t u = (uint32_t)b << 16;
+        float f;
+        std::memcpy(&f, &u, 4);
+        return (double)f;
+    }
+    __half_raw hr;
+    hr.x = b;
+    return (double)__half2float(__half(hr));
+}
+
+// Validate a host CSR, copy it and its plan(s) to the device.  Graph offsets
+// (for batched handles) are filled in by the caller.
+static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t* row_ptr,
+                       const int32_t* col_idx, const void* values, spmm_dtype vtype, uint32_t flags,
+                       const spmm_opts* opts, cudaStream_t s, const char* who) {
+    const std::string w(who);
+    if (!out) { set_error(w + ": out is NULL"); return SPMM_ERR_ARG; }
     if (n_rows < 0 || n_rows >= (int64_t)1 << 31 || n_cols < 1 || n_cols >= (int64_t)1 << 31 || nnz < 0) {
-        set_error("spmm_create_csr: need 0 <= n_rows < 2^31, 1 <= n_cols < 2^31, nnz >= 0");
+        set_error(w + ": need 0 <= n_rows < 2^31, 1 <= n_cols < 2^31, nnz >= 0");
         return SPMM_ERR_ARG;
     }
-    if (!row_ptr || (nnz > 0 && !col_idx)) { set_error("spmm_create_csr: row_ptr/col_idx is NULL"); return SPMM_ERR_ARG; }
-    if (flags & ~SPMM_WANT_TRANSPOSE) { set_error("spmm_create_csr: unknown flag bits"); return SPMM_ERR_ARG; }
+    if (!row_ptr || (nnz > 0 && !col_idx)) { set_error(w + ": row_ptr/col_idx is NULL"); return SPMM_ERR_ARG; }
+    if (flags & ~SPMM_WANT_TRANSPOSE) { set_error(w + ": unknown flag bits"); return SPMM_ERR_ARG; }
     size_t vsize = 0;
     if (values) {
         if (vtype != SPMM_F32 && vtype != SPMM_BF16 && vtype != SPMM_F16) {
-            set_error("spmm_create_csr: values must be F32, BF16 or F16");
+            set_error(w + ": values must be F32, BF16 or F16");
             return SPMM_ERR_ARG;
         }
         vsize = dtype_size(vtype);
     }
     // ---- validate the CSR structure
-    if (row_ptr[0] != 0) { set_error("spmm_create_csr: row_ptr[0] != 0"); return SPMM_ERR_FORMAT; }
-    if (row_ptr[n_rows] != nnz) { set_error("spmm_create_csr: row_ptr[n_rows] != nnz"); return SPMM_ERR_FORMAT; }
+    if (row_ptr[0] != 0) { set_error(w + ": row_ptr[0] != 0"); return SPMM_ERR_FORMAT; }
+    if (row_ptr[n_rows] != nnz) { set_error(w + ": row_ptr[n_rows] != nnz"); return SPMM_ERR_FORMAT; }
     for (int64_t i = 0; i < n_rows; ++i)
         if (row_ptr[i + 1] < row_ptr[i]) {
-            set_error("spmm_create_csr: row_ptr decreases at row " + std::to_string(i));
+            set_error(w + ": row_ptr decreases at row " + std::to_string(i));
             return SPMM_ERR_FORMAT;
         }
     for (int64_t p = 0; p < nnz; ++p)
         if (col_idx[p] < 0 || (int64_t)col_idx[p] >= n_cols) {
-            set_error("spmm_create_csr: column index out of range at entry " + std::to_string(p));
+            set_error(w + ": column index out of range at entry " + std::to_string(p));
             return SPMM_ERR_FORMAT;
         }
     const Params prm = resolve_params(opts);
 
     spmm_mat* A = new (std::nothrow) spmm_mat();
-    if (!A) { set_error("spmm_create_csr: out of host memory"); return SPMM_ERR_OOM; }
+    if (!A) { set_error(w + ": out of host memory"); return SPMM_ERR_OOM; }
     A->params = prm;
     A->vtype = values ? (int32_t)vtype : -1;
-    cudaStream_t s = (cudaStream_t)stream;
+    A->row_off = {0, n_rows};
+    A->col_off = {0, n_cols};
+    double a2 = 0.0;
+    for (int64_t p = 0; p < nnz; ++p) {
+        const double v = host_value(values, vtype, p);
+        a2 += v * v;
+    }
+    A->a2 = {a2};
     cudaError_t se = cudaMalloc((void**)&A->status, sizeof(int32_t));
     if (se == cudaSuccess) se = cudaMemsetAsync(A->status, 0, sizeof(int32_t), s);
     if (se != cudaSuccess) {
         cudaFree(A->status);
         delete A;
-        return cuda_fail(se, "spmm_create_csr: status word");
+        return cuda_fail(se, (w + ": status word").c_str());
     }
     int rc = build_orientation(A->fwd, n_rows, n_cols, row_ptr, col_idx, values, vsize, prm, s, &A->device_bytes);
     if (rc == SPMM_OK && (flags & SPMM_WANT_TRANSPOSE)) {
@@ -204,7 +233,7 @@ extern "C" int spmm_create_csr(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, 
             if (values) tval.resize((size_t)nnz * vsize);
         } catch (const std::bad_alloc&) {
             rc = SPMM_ERR_OOM;
-            set_error("spmm_create_csr: out of host memory for the transpose");
+            set_error(w + ": out of host memory for the transpose");
         }
         if (rc == SPMM_OK) {
             for (int64_t p = 0; p < nnz; ++p) tptr[(size_t)col_idx[p] + 1]++;
@@ -228,6 +257,93 @@ extern "C" int spmm_create_csr(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, 
         delete A;
         return rc;
     }
+    *out = A;
+    return SPMM_OK;
+}
+
+}  // namespace spmm
+
+extern "C" int spmm_create_csr(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, int64_t nnz,
+                               const int64_t* row_ptr, const int32_t* col_idx, const void* values,
+                               spmm_dtype vtype, uint32_t flags, const spmm_opts* opts, void* stream) {
+    set_error("");
+    return create_impl(out, n_rows, n_cols, nnz, row_ptr, col_idx, values, vtype, flags, opts,
+                       (cudaStream_t)stream, "spmm_create_csr");
+}
+
+extern "C" int spmm_create_batched(spmm_mat_t* out, int32_t n_graphs, const int64_t* n_rows, const int64_t* n_cols,
+                                   const int64_t* const* row_ptrs, const int32_t* const* col_idxs,
+                                   const void* const* values, spmm_dtype vtype, uint32_t flags,
+                                   const spmm_opts* opts, void* stream) {
+    set_error("");
+    if (!out || n_graphs < 1 || !n_rows || !n_cols || !row_ptrs || !col_idxs) {
+        set_error("spmm_create_batched: NULL argument or n_graphs < 1");
+        return SPMM_ERR_ARG;
+    }
+    const size_t vsize = values ? dtype_size(vtype) : 0;
+    std::vector<int64_t> roff((size_t)n_graphs + 1, 0), coff((size_t)n_graphs + 1, 0);
+    int64_t nnz = 0;
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        if (n_rows[g] < 0 || n_cols[g] < 1 || !row_ptrs[g] || (values && !values[g])) {
+            set_error("spmm_create_batched: bad size or NULL array for graph " + std::to_string(g));
+            return SPMM_ERR_ARG;
+        }
+        const int64_t* rp = row_ptrs[g];
+        if (rp[0] != 0) { set_error("spmm_create_batched: row_ptr[0] != 0 in graph " + std::to_string(g)); return SPMM_ERR_FORMAT; }
+        for (int64_t i = 0; i < n_rows[g]; ++i)
+            if (rp[i + 1] < rp[i]) {
+                set_error("spmm_create_batched: row_ptr decreases in graph " + std::to_string(g));
+                return SPMM_ERR_FORMAT;
+            }
+        const int64_t z = rp[n_rows[g]];
+        if (z > 0 && !col_idxs[g]) { set_error("spmm_create_batched: col_idx is NULL"); return SPMM_ERR_ARG; }
+        for (int64_t p = 0; p < z; ++p)
+            if (col_idxs[g][p] < 0 || col_idxs[g][p] >= n_cols[g]) {
+                set_error("spmm_create_batched: column index out of range in graph " + std::to_string(g));
+                return SPMM_ERR_FORMAT;
+            }
+        roff[g + 1] = roff[g] + n_rows[g];
+        coff[g + 1] = coff[g] + n_cols[g];
+        nnz += z;
+    }
+    if (roff[n_graphs] >= (int64_t)1 << 31 || coff[n_graphs] >= (int64_t)1 << 31) {
+        set_error("spmm_create_batched: more than 2^31 rows or columns in the batch");
+        return SPMM_ERR_ARG;
+    }
+    // block-diagonal CSR of the whole batch
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<char> va;
+    try {
+        rp.resize((size_t)roff[n_graphs] + 1);
+        ci.resize((size_t)nnz);
+        if (values) va.resize((size_t)nnz * vsize);
+    } catch (const std::bad_alloc&) {
+        set_error("spmm_create_batched: out of host memory");
+        return SPMM_ERR_OOM;
+    }
+    int64_t e = 0;
+    std::vector<double> a2((size_t)n_graphs, 0.0);
+    rp[0] = 0;
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        const int64_t z = row_ptrs[g][n_rows[g]];
+        for (int64_t i = 0; i < n_rows[g]; ++i) rp[(size_t)(roff[g] + i + 1)] = e + row_ptrs[g][i + 1];
+        for (int64_t p = 0; p < z; ++p) ci[(size_t)(e + p)] = (int32_t)(col_idxs[g][p] + coff[g]);
+        if (values) std::memcpy(&va[(size_t)e * vsize], values[g], (size_t)z * vsize);
+        for (int64_t p = 0; p < z; ++p) {
+            const double v = values ? host_value(values[g], vtype, p) : 1.0;
+            a2[(size_t)g] += v * v;
+        }
+        e += z;
+    }
+    spmm_mat* A = nullptr;
+    const int rc = create_impl(&A, roff[n_graphs], coff[n_graphs], nnz, rp.data(), ci.data(),
+                               values ? va.data() : nullptr, vtype, flags, opts, (cudaStream_t)stream,
+                               "spmm_create_batched");
+    if (rc != SPMM_OK) return rc;
+    A->row_off = roff;
+    A->col_off = coff;
+    A->a2 = a2;
     *out = A;
     return SPMM_OK;
 }
@@ -330,6 +446,7 @@ extern "C" int spmm_get_info(spmm_mat_t A, spmm_info* info) {
     info->device_bytes = A->device_bytes;
     info->value_dtype = A->vtype;
     info->has_transpose = A->has_tr ? 1 : 0;
+    info->n_graphs = (int32_t)(A->row_off.size() - 1);
     return SPMM_OK;
 }
 

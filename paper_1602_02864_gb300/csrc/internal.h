@@ -72,6 +72,10 @@ struct spmm_mat {
     spmm::Params params;
     int64_t device_bytes = 0;
     int32_t* status = nullptr;  // device word: nonzero after a timed-out wait
+    // batch layout (one graph for spmm_create_csr): graph g owns rows
+    // row_off[g] .. row_off[g+1]-1 and columns col_off[g] .. col_off[g+1]-1
+    std::vector<int64_t> row_off, col_off;
+    std::vector<double> a2;     // ||A_g||_F^2 per graph
 };
 
 namespace spmm {

@@ -41,7 +41,8 @@ class spmm_opts(ctypes.Structure):
 class spmm_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("n_rows", "n_cols", "nnz", "n_tasks", "n_split_rows", "n_segments",
                                               "n_tasks_t", "n_split_rows_t", "n_segments_t", "device_bytes")] + [
-        ("value_dtype", ctypes.c_int32), ("has_transpose", ctypes.c_int32)]
+        ("value_dtype", ctypes.c_int32), ("has_transpose", ctypes.c_int32), ("n_graphs", ctypes.c_int32),
+        ("reserved", ctypes.c_int32)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -73,6 +74,11 @@ _lib.spmm_apply_csr_static.argtypes = [_i64, _i64, _i64, _P, _P, _P, ctypes.c_in
 _lib.spmm_apply_csr_static.restype = ctypes.c_int
 _lib.spmm_pagerank.argtypes = [_P, ctypes.c_double, _i32, _P, _P, _P, _P]
 _lib.spmm_pagerank.restype = ctypes.c_int
+_lib.spmm_create_batched.argtypes = [ctypes.POINTER(_P), _i32, _P, _P, _P, _P, _P, ctypes.c_int, _u32,
+                                     ctypes.POINTER(spmm_opts), _P]
+_lib.spmm_create_batched.restype = ctypes.c_int
+_lib.spmm_nmf.argtypes = [_P, _i32, _i32, _P, _P, ctypes.c_int, ctypes.c_double, _P, _P]
+_lib.spmm_nmf.restype = ctypes.c_int
 _lib.spmm_last_error.argtypes = []
 _lib.spmm_last_error.restype = ctypes.c_char_p
 
@@ -194,6 +200,35 @@ def spmm_pagerank(h, damping, iters, x, x0=None, stream=None) -> np.ndarray:
     return res[:int(iters)]
 
 
+def spmm_create_batched(graphs, flags=0, opts: spmm_opts | None = None, stream=None, weighted=True) -> _P:
+    """One block-diagonal handle for a list of host CSR graphs (objects with
+    n_rows, n_cols, row_ptr, col_idx, values)."""
+    n = len(graphs)
+    nr = np.array([g.n_rows for g in graphs], dtype=np.int64)
+    nc = np.array([g.n_cols for g in graphs], dtype=np.int64)
+    rps = [np.ascontiguousarray(g.row_ptr, dtype=np.int64) for g in graphs]
+    cis = [np.ascontiguousarray(g.col_idx, dtype=np.int32) for g in graphs]
+    rp_arr = (_P * n)(*[_P(a.ctypes.data) for a in rps])
+    ci_arr = (_P * n)(*[_P(a.ctypes.data) for a in cis])
+    use_vals = weighted and all(g.values is not None for g in graphs)
+    vals = [np.ascontiguousarray(g.values, dtype=np.float32) for g in graphs] if use_vals else None
+    v_arr = (_P * n)(*[_P(a.ctypes.data) for a in vals]) if use_vals else None
+    h = _P(0)
+    _check(_lib.spmm_create_batched(ctypes.byref(h), n, _ptr(nr), _ptr(nc), rp_arr, ci_arr, v_arr, SPMM_F32,
+                                    int(flags), ctypes.byref(opts) if opts is not None else None,
+                                    _stream_handle(stream)))
+    return h
+
+
+def spmm_nmf(h, k, steps, W, Ht, ftype=SPMM_F32, eps=1e-12, n_graphs=1, stream=None) -> np.ndarray:
+    """NMF in place on float32 CUDA tensors W, Ht; returns objective
+    [n_graphs, steps+1] (FP64)."""
+    obj = np.zeros((n_graphs, int(steps) + 1), dtype=np.float64)
+    _check(_lib.spmm_nmf(h, int(k), int(steps), _ptr(W), _ptr(Ht), int(ftype), float(eps), _P(obj.ctypes.data),
+                         _stream_handle(stream)))
+    return obj
+
+
 def spmm_get_info(h) -> dict:
     info = spmm_info()
     _check(_lib.spmm_get_info(h, ctypes.byref(info)))
@@ -212,6 +247,19 @@ class SparseMatrix:
         self.n_rows, self.n_cols = int(n_rows), int(n_cols)
         self.handle = spmm_create_csr(n_rows, n_cols, row_ptr, col_idx, values,
                                       SPMM_WANT_TRANSPOSE if transpose else 0, opts, stream)
+
+    @classmethod
+    def batched(cls, graphs, transpose=False, weighted=True, opts: spmm_opts | None = None, stream=None):
+        """Block-diagonal handle over a list of graphs (one launch per apply)."""
+        self = cls.__new__(cls)
+        self.n_rows = int(sum(g.n_rows for g in graphs))
+        self.n_cols = int(sum(g.n_cols for g in graphs))
+        self.handle = spmm_create_batched(graphs, SPMM_WANT_TRANSPOSE if transpose else 0, opts, stream, weighted)
+        return self
+
+    def nmf(self, k, steps, W, Ht, ftype=SPMM_F32, eps=1e-12, stream=None):
+        """NMF in place on W (rows x k) and Ht (cols x k); returns objective."""
+        return spmm_nmf(self.handle, k, steps, W, Ht, ftype, eps, self.info()["n_graphs"], stream)
 
     @classmethod
     def from_csr(cls, A, transpose=False, values=None, **kw):

@@ -1,0 +1,113 @@
+"""Batched (block-diagonal) SpMM and NMF (Section 4.3) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import abs_product, assert_close_rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sp():
+    from paper_1602_02864_gb300 import spmm
+    return spmm
+
+
+@pytest.fixture(scope="module")
+def batch():
+    graphs = []
+    for g in range(6):
+        A = synth.chunglu_csr(g, seed=3, nmin=300, nmax=4000)
+        A.values = synth.uniform01(A.nnz, seed=3, seed2=g)
+        graphs.append(A)
+    return graphs
+
+
+@pytest.mark.parametrize("k", [1, 8, 13])
+def test_batched_spmm_matches_per_graph_oracle(sp, batch, k):
+    import torch
+    h = sp.SparseMatrix.batched(batch, transpose=True)
+    assert h.info()["n_graphs"] == len(batch)
+    for tr in (False, True):
+        xs = [synth.dense(A.n_rows if tr else A.n_cols, k, seed=i) for i, A in enumerate(batch)]
+        Y = h.apply(torch.from_numpy(np.concatenate(xs)).cuda(), transpose=tr).cpu().numpy()
+        off = 0
+        for A, X in zip(batch, xs):
+            n_out = A.n_cols if tr else A.n_rows
+            ref = oracle.spmm(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.values, X, transpose=tr)
+            assert_close_rel(Y[off:off + n_out], ref, abs_product(A, X.astype(np.float64), tr), 1e-5, "batched")
+            off += n_out
+        assert off == Y.shape[0]
+    h.close()
+
+
+def _init(n, k, seed):
+    return synth.dense(n, k, seed=seed, mode="unit") + np.float32(0.01)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_nmf_single_graph_matches_oracle(sp, weighted):
+    import torch
+    A = synth.chunglu_csr(1, seed=5, nmin=1500, nmax=1600)
+    if weighted:
+        A.values = synth.uniform01(A.nnz, seed=5)
+    k, steps = 8, 30
+    W0, H0 = _init(A.n_rows, k, 1), _init(A.n_cols, k, 2)
+    h = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.values, transpose=True)
+    W, Ht = torch.from_numpy(W0.copy()).cuda(), torch.from_numpy(H0.copy()).cuda()
+    obj = h.nmf(k, steps, W, Ht)[0]
+    Wr, Hr, objr = oracle.nmf(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.values, W0, H0, steps)
+    np.testing.assert_allclose(obj, objr, rtol=1e-4)
+    np.testing.assert_allclose(W.cpu().numpy(), Wr, rtol=1e-2, atol=1e-4 * np.abs(Wr).max())
+    np.testing.assert_allclose(Ht.cpu().numpy(), Hr, rtol=1e-2, atol=1e-4 * np.abs(Hr).max())
+    assert np.all(np.diff(obj) <= 1e-6 * obj[:-1])
+    assert W.min().item() >= 0 and Ht.min().item() >= 0
+    h.close()
+
+
+def test_nmf_batched_per_graph(sp, batch):
+    import torch
+    k, steps = 8, 20
+    h = sp.SparseMatrix.batched(batch, transpose=True, weighted=False)
+    W0 = [_init(A.n_rows, k, 10 + i) for i, A in enumerate(batch)]
+    H0 = [_init(A.n_cols, k, 20 + i) for i, A in enumerate(batch)]
+    W = torch.from_numpy(np.concatenate(W0)).cuda()
+    Ht = torch.from_numpy(np.concatenate(H0)).cuda()
+    obj = h.nmf(k, steps, W, Ht)
+    assert obj.shape == (len(batch), steps + 1)
+    for i, A in enumerate(batch):
+        _, _, objr = oracle.nmf(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, W0[i], H0[i], steps)
+        np.testing.assert_allclose(obj[i], objr, rtol=1e-4)
+    # determinism
+    W2 = torch.from_numpy(np.concatenate(W0)).cuda()
+    H2 = torch.from_numpy(np.concatenate(H0)).cuda()
+    obj2 = h.nmf(k, steps, W2, H2)
+    assert np.array_equal(obj, obj2) and torch.equal(W, W2)
+    h.close()
+
+
+def test_nmf_bf16_factors(sp):
+    import torch
+    A = synth.chunglu_csr(2, seed=7, nmin=3000, nmax=3100)
+    k, steps = 16, 25
+    W0, H0 = _init(A.n_rows, k, 3), _init(A.n_cols, k, 4)
+    h = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, transpose=True)
+    of = h.nmf(k, steps, torch.from_numpy(W0.copy()).cuda(), torch.from_numpy(H0.copy()).cuda())[0]
+    ob = h.nmf(k, steps, torch.from_numpy(W0.copy()).cuda(), torch.from_numpy(H0.copy()).cuda(),
+               ftype=sp.SPMM_BF16)[0]
+    np.testing.assert_allclose(ob, of, rtol=1e-2)
+    assert ob[-1] < ob[0] and np.all(np.diff(ob) <= 1e-3 * ob[:-1])
+    h.close()
+
+
+def test_nmf_argument_errors(sp):
+    import torch
+    A = synth.chunglu_csr(0, seed=1, nmin=200, nmax=300)
+    h = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None)       # no transpose
+    W = torch.ones((A.n_rows, 4), device="cuda")
+    H = torch.ones((A.n_cols, 4), device="cuda")
+    with pytest.raises(sp.SpmmError):
+        h.nmf(4, 3, W, H)
+    h.close()

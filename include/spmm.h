@@ -277,6 +277,35 @@ int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float* x, const f
 int spmm_nmf(spmm_mat_t A, int32_t k, int32_t steps, float* W, float* Ht, spmm_dtype ftype, double eps,
              double* objective, void* stream);
 
+/*
+ * spmm_eigs -- the nev largest (algebraic) eigenpairs of a symmetric matrix
+ * S by a thick-restart block Krylov method (the symmetric form of the block
+ * Krylov-Schur solver of Section 4.2, whose only sparse operation is the block
+ * product S V).  The basis and S V are FP64; each expansion multiplies the
+ * newest block by S with X in FP32 or BF16 (FP32 accumulation); Gram-Schmidt
+ * (twice), CholQR2 and Rayleigh-Ritz are FP64; a restart keeps nev + block
+ * Ritz vectors.
+ *   S            square handle of a symmetric matrix (values F32, BF16 or none)
+ *   nev          eigenpairs wanted
+ *   block        block size (1..32)
+ *   max_basis    basis size, nev + 2*block <= max_basis <= min(64, n)
+ *   max_restarts restarts before giving up (the best pairs are returned)
+ *   tol          stop when every wanted pair has ||S u - theta u||_2 <= tol (unit u)
+ *   xtype        SPMM_F32 or SPMM_BF16: type of the block fed to the SpMM
+ *   V0           device double[n * block], row-major start block (full rank)
+ *   evals        host double[nev], descending
+ *   evecs        device double[n * nev] row-major (unit columns), or NULL
+ *   resid        host double[nev] residual norms, or NULL
+ *   restarts_out host int32 restarts used, or NULL
+ * Synchronises `stream`; runs on an internal stream; allocates its workspace
+ * (about 6 * n * max_basis doubles).  Errors: SPMM_ERR_ARG (sizes, NULL,
+ * rank-deficient start block), SPMM_ERR_UNSUPPORTED, SPMM_ERR_TIMEOUT,
+ * SPMM_ERR_OOM, SPMM_ERR_CUDA.
+ */
+int spmm_eigs(spmm_mat_t S, int32_t nev, int32_t block, int32_t max_basis, int32_t max_restarts, double tol,
+              spmm_dtype xtype, const double* V0, double* evals, double* evecs, double* resid,
+              int32_t* restarts_out, void* stream);
+
 /* spmm_get_info -- plan statistics of a handle (host call, no GPU work). */
 int spmm_get_info(spmm_mat_t A, spmm_info* info);
 

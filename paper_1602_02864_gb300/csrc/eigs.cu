@@ -1,0 +1,405 @@
+// eigs.cu -- block eigensolver on the SpMM path (paper Section 4.2).
+//
+// Section 4.2 runs a block Krylov-Schur eigensolver whose only sparse
+// operation is the block product S V.  This is a thick-restart block Krylov
+// method for a symmetric S (for symmetric matrices Krylov-Schur restarting is
+// thick-restart Lanczos): the basis V and S V are held in FP64; every
+// expansion multiplies the newest block by S through the task kernel (X =
+// the block in FP32 or BF16, FP32 accumulation, converted back to FP64);
+// orthogonalisation is block classical Gram-Schmidt applied twice followed by
+// CholQR2, all in FP64; the Rayleigh-Ritz problem T = V^T (S V) is solved on
+// the host in FP64 by cyclic Jacobi; a restart keeps the best nev + block Ritz
+// vectors and their images, and the next expansion starts from S applied to
+// the kept Ritz vectors (whose components orthogonal to V are the residuals).
+//
+// Tall-skinny FP64 kernels: C = A^T B (chunked partials added in a fixed
+// order) and Out = beta Out + alpha A C (one thread per output element).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace spmm {
+
+constexpr int kEigThreads = 256;
+constexpr int kEigMaxBasis = 64;
+constexpr int kTsTile = 16;
+
+// partial[c][r*q + s] = sum over chunk rows i of A[i][r] * B[i][s]
+__global__ void __launch_bounds__(kEigThreads)
+ts_tn_partial_kernel(const double* __restrict__ A, int64_t lda, int p, const double* __restrict__ B, int64_t ldb,
+                     int q, int64_t n, int64_t chunk, double* __restrict__ partial) {
+    __shared__ double ta[kTsTile * kEigMaxBasis];
+    __shared__ double tb[kTsTile * kEigMaxBasis];
+    const int pq = p * q;
+    const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    double acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+    for (int64_t r0 = i0; r0 < i1; r0 += kTsTile) {
+        const int rows = (int)min((int64_t)kTsTile, i1 - r0);
+        for (int t = threadIdx.x; t < rows * p; t += blockDim.x) ta[t] = A[(r0 + t / p) * lda + t % p];
+        for (int t = threadIdx.x; t < rows * q; t += blockDim.x) tb[t] = B[(r0 + t / q) * ldb + t % q];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int e = threadIdx.x + j * kEigThreads;
+            if (e < pq) {
+                const int r = e / q, s = e % q;
+                double f = 0.0;
+                for (int t = 0; t < rows; ++t) f = fma(ta[t * p + r], tb[t * q + s], f);
+                acc[j] += f;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int e = threadIdx.x + j * kEigThreads;
+        if (e < pq) partial[(int64_t)blockIdx.x * pq + e] = acc[j];
+    }
+}
+
+__global__ void ts_reduce_kernel(const double* __restrict__ partial, int nparts, int pq, double* __restrict__ out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < pq; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < nparts; ++c) s += partial[(int64_t)c * pq + e];
+        out[e] = s;
+    }
+}
+
+// Out[i][j] = beta * Out[i][j] + alpha * sum_r A[i][r] * C[r][j]   (C is p x q, row-major)
+__global__ void __launch_bounds__(kEigThreads)
+ts_nn_kernel(const double* __restrict__ A, int64_t lda, int p, const double* __restrict__ C, int q, double* Out,
+             int64_t ldo, int64_t n, double alpha, double beta) {
+    __shared__ double cs[kEigMaxBasis * kEigMaxBasis];
+    for (int t = threadIdx.x; t < p * q; t += blockDim.x) cs[t] = C[t];
+    __syncthreads();
+    const int64_t total = n * q;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / q;
+        const int j = (int)(t % q);
+        double s = 0.0;
+        for (int r = 0; r < p; ++r) s = fma(A[i * lda + r], cs[r * q + j], s);
+        Out[i * ldo + j] = (beta == 0.0 ? 0.0 : beta * Out[i * ldo + j]) + alpha * s;
+    }
+}
+
+// strided FP64 block -> contiguous FP32 or BF16 (SpMM input)
+__global__ void f64_to_x_kernel(const double* __restrict__ src, int64_t lds, int b, int64_t n, void* dst, int bf16) {
+    const int64_t total = n * b;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const double v = src[(t / b) * lds + t % b];
+        if (bf16) static_cast<__nv_bfloat16*>(dst)[t] = __double2bfloat16(v);
+        else static_cast<float*>(dst)[t] = (float)v;
+    }
+}
+
+// contiguous FP32 (SpMM output) -> strided FP64 block
+__global__ void f32_to_f64_kernel(const float* __restrict__ src, int b, int64_t n, double* dst, int64_t ldd) {
+    const int64_t total = n * b;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+        dst[(t / b) * ldd + t % b] = (double)src[t];
+}
+
+// strided FP64 copy of an n x b block
+__global__ void copy_block_kernel(const double* __restrict__ src, int64_t lds, int b, int64_t n, double* dst,
+                                  int64_t ldd) {
+    const int64_t total = n * b;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+        dst[(t / b) * ldd + t % b] = src[(t / b) * lds + t % b];
+}
+
+// residual block R = AU - U diag(theta)
+__global__ void residual_kernel(const double* __restrict__ AU, const double* __restrict__ U, const double* theta,
+                                int q, int64_t n, double* R) {
+    const int64_t total = n * q;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+        R[t] = AU[t] - theta[t % q] * U[t];
+}
+
+// ---------------------------------------------------------------- host linear algebra
+// Cholesky G = R^T R (R upper); false if a pivot is not safely positive.
+static bool cholesky_upper(int b, const std::vector<double>& G, std::vector<double>& R) {
+    R.assign((size_t)b * b, 0.0);
+    double tr = 0.0;
+    for (int i = 0; i < b; ++i) tr += G[(size_t)i * b + i];
+    for (int j = 0; j < b; ++j) {
+        double d = G[(size_t)j * b + j];
+        for (int k = 0; k < j; ++k) d -= R[(size_t)k * b + j] * R[(size_t)k * b + j];
+        if (!(d > 1e-24 * (tr > 0 ? tr : 1.0))) return false;
+        const double rjj = std::sqrt(d);
+        R[(size_t)j * b + j] = rjj;
+        for (int i = j + 1; i < b; ++i) {
+            double s = G[(size_t)j * b + i];
+            for (int k = 0; k < j; ++k) s -= R[(size_t)k * b + j] * R[(size_t)k * b + i];
+            R[(size_t)j * b + i] = s / rjj;
+        }
+    }
+    return true;
+}
+
+// inverse of an upper-triangular b x b matrix
+static std::vector<double> upper_inverse(int b, const std::vector<double>& R) {
+    std::vector<double> X((size_t)b * b, 0.0);
+    for (int j = 0; j < b; ++j) {
+        X[(size_t)j * b + j] = 1.0 / R[(size_t)j * b + j];
+        for (int i = j - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int k = i + 1; k <= j; ++k) s += R[(size_t)i * b + k] * X[(size_t)k * b + j];
+            X[(size_t)i * b + j] = -s / R[(size_t)i * b + i];
+        }
+    }
+    return X;
+}
+
+// cyclic Jacobi eigen-decomposition of a symmetric m x m matrix (destroyed);
+// column c of V is the eigenvector of evals[c]
+static void jacobi_eigh(int m, std::vector<double>& M, std::vector<double>& evals, std::vector<double>& V) {
+    V.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) V[(size_t)i * m + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                const double x = M[(size_t)i * m + j];
+                tot += x * x;
+                if (i != j) off += x * x;
+            }
+        if (off == 0.0 || off <= 1e-30 * tot) break;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                const double apq = M[(size_t)p * m + q];
+                if (apq == 0.0) continue;
+                const double theta = (M[(size_t)q * m + q] - M[(size_t)p * m + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int r = 0; r < m; ++r) {
+                    const double a = M[(size_t)r * m + p], b = M[(size_t)r * m + q];
+                    M[(size_t)r * m + p] = c * a - s * b;
+                    M[(size_t)r * m + q] = s * a + c * b;
+                }
+                for (int r = 0; r < m; ++r) {
+                    const double a = M[(size_t)p * m + r], b = M[(size_t)q * m + r];
+                    M[(size_t)p * m + r] = c * a - s * b;
+                    M[(size_t)q * m + r] = s * a + c * b;
+                }
+                for (int r = 0; r < m; ++r) {
+                    const double a = V[(size_t)r * m + p], b = V[(size_t)r * m + q];
+                    V[(size_t)r * m + p] = c * a - s * b;
+                    V[(size_t)r * m + q] = s * a + c * b;
+                }
+            }
+    }
+    evals.resize(m);
+    for (int i = 0; i < m; ++i) evals[i] = M[(size_t)i * m + i];
+}
+
+namespace {
+
+struct Eig {
+    const spmm_mat* A;
+    int64_t n;
+    int m, b;
+    int xtype;
+    cudaStream_t s;
+    double *V = nullptr, *AV = nullptr, *W = nullptr, *W2 = nullptr, *part = nullptr, *small = nullptr;
+    double *U = nullptr, *AU = nullptr, *theta = nullptr;
+    float* Yf = nullptr;
+    void* Xs = nullptr;
+    int64_t chunk = 0;
+    int nchunks = 0;
+    int grid = 0;
+
+    cudaError_t tn(const double* Am, int64_t lda, int p, const double* Bm, int64_t ldb, int q, std::vector<double>& out) {
+        ts_tn_partial_kernel<<<nchunks, kEigThreads, 0, s>>>(Am, lda, p, Bm, ldb, q, n, chunk, part);
+        ts_reduce_kernel<<<(p * q + 255) / 256, 256, 0, s>>>(part, nchunks, p * q, small);
+        out.resize((size_t)p * q);
+        cudaError_t e = cudaMemcpyAsync(out.data(), small, (size_t)p * q * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e;
+    }
+    cudaError_t nn(const double* Am, int64_t lda, int p, const std::vector<double>& C, int q, double* Out, int64_t ldo,
+                   double alpha, double beta) {
+        cudaError_t e = cudaMemcpyAsync(small, C.data(), (size_t)p * q * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        ts_nn_kernel<<<grid, kEigThreads, 0, s>>>(Am, lda, p, small, q, Out, ldo, n, alpha, beta);
+        // small is reused by the next call: finish this one first
+        return cudaStreamSynchronize(s);
+    }
+    // Y = S * block (block: n x b FP64 with leading dimension ld) into out (ld m)
+    int apply_block(const double* blk, int64_t ld, double* out, int64_t ldo) {
+        f64_to_x_kernel<<<grid, kEigThreads, 0, s>>>(blk, ld, b, n, Xs, xtype == SPMM_BF16);
+        const int rc = apply_dev(A, 0, Xs, b, b, xtype, Yf, b, s);
+        if (rc != SPMM_OK) return rc;
+        f32_to_f64_kernel<<<grid, kEigThreads, 0, s>>>(Yf, b, n, out, ldo);
+        return SPMM_OK;
+    }
+    // orthonormalise W (n x b) against V[:, :cur] twice, then CholQR2; false on breakdown
+    bool orthonormalize(int cur, cudaError_t& e) {
+        std::vector<double> C, G, R;
+        for (int pass = 0; pass < 2 && cur > 0; ++pass) {
+            if ((e = tn(V, m, cur, W, b, b, C)) != cudaSuccess) return false;
+            if ((e = nn(V, m, cur, C, b, W, b, -1.0, 1.0)) != cudaSuccess) return false;
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+            if ((e = tn(W, b, b, W, b, b, G)) != cudaSuccess) return false;
+            if (!cholesky_upper(b, G, R)) return false;
+            const std::vector<double> Ri = upper_inverse(b, R);
+            if ((e = nn(W, b, b, Ri, b, W2, b, 1.0, 0.0)) != cudaSuccess) return false;
+            std::swap(W, W2);
+        }
+        return true;
+    }
+};
+
+}  // namespace
+
+}  // namespace spmm
+
+using namespace spmm;
+
+extern "C" int spmm_eigs(spmm_mat_t S, int32_t nev, int32_t block, int32_t max_basis, int32_t max_restarts,
+                         double tol, spmm_dtype xtype, const double* V0, double* evals, double* evecs,
+                         double* resid, int32_t* restarts_out, void* stream) {
+    if (!S || !V0 || !evals) { set_error("spmm_eigs: NULL argument"); return SPMM_ERR_ARG; }
+    const int64_t n = S->fwd.n_rows;
+    if (S->fwd.n_cols != n || n < 1) { set_error("spmm_eigs: the matrix must be square"); return SPMM_ERR_ARG; }
+    if (block < 1 || block > 32 || nev < 1 || nev > block + 32 || max_basis > kEigMaxBasis ||
+        max_basis < nev + 2 * block || max_basis > n || max_restarts < 0 || !(tol > 0.0)) {
+        set_error("spmm_eigs: need 1 <= block <= 32, nev + 2*block <= max_basis <= min(64, n), max_restarts >= 0, "
+                  "tol > 0");
+        return SPMM_ERR_ARG;
+    }
+    if (xtype != SPMM_F32 && xtype != SPMM_BF16) { set_error("spmm_eigs: xtype must be F32 or BF16"); return SPMM_ERR_ARG; }
+    if (S->vtype == SPMM_F16 || (S->vtype == SPMM_BF16 && xtype != SPMM_BF16)) {
+        set_error("spmm_eigs: 16-bit values need X of the same type (use F32 values)");
+        return SPMM_ERR_UNSUPPORTED;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    Eig E;
+    E.A = S;
+    E.n = n;
+    E.m = max_basis;
+    E.b = block;
+    E.xtype = xtype;
+    E.grid = std::max(1, sms * 8);
+    E.chunk = std::max<int64_t>(1024, (n + 1023) / 1024);
+    E.nchunks = (int)((n + E.chunk - 1) / E.chunk);
+    const int m = max_basis, b = block;
+    const int keep = std::min(nev + b, m - b);
+    int rc = SPMM_OK;
+    cudaError_t e = cudaSuccess;
+    auto fail = [&](cudaError_t err, const char* what) { rc = cuda_fail(err, what); };
+    do {
+        if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess) { fail(e, "spmm_eigs: stream"); break; }
+        if ((e = cudaStreamCreateWithFlags(&E.s, cudaStreamNonBlocking)) != cudaSuccess) { fail(e, "spmm_eigs: stream"); break; }
+        const size_t nm = (size_t)n * m * sizeof(double);
+        if ((e = cudaMalloc((void**)&E.V, nm)) != cudaSuccess || (e = cudaMalloc((void**)&E.AV, nm)) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.U, nm)) != cudaSuccess || (e = cudaMalloc((void**)&E.AU, nm)) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.W, (size_t)n * m * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.W2, (size_t)n * m * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.part, (size_t)E.nchunks * m * m * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.small, (size_t)m * m * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.theta, (size_t)m * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.Yf, (size_t)n * b * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&E.Xs, (size_t)n * b * sizeof(float))) != cudaSuccess) {
+            fail(e, "spmm_eigs: workspace");
+            break;
+        }
+        // start block
+        copy_block_kernel<<<E.grid, kEigThreads, 0, E.s>>>(V0, b, b, n, E.W, b);
+        if (!E.orthonormalize(0, e)) {
+            if (e != cudaSuccess) fail(e, "spmm_eigs: orthonormalise");
+            else { set_error("spmm_eigs: the start block is rank-deficient"); rc = SPMM_ERR_ARG; }
+            break;
+        }
+        copy_block_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.W, b, b, n, E.V, m);
+        if ((rc = E.apply_block(E.V, m, E.AV, m)) != SPMM_OK) break;
+        int cur = b, seed = 0, restarts = 0;
+        std::vector<double> T, th, Y, Rn;
+        bool done = false;
+        while (!done) {
+            // ---- expand the basis block by block
+            while (cur + b <= m) {
+                copy_block_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.AV + seed, m, b, n, E.W, b);
+                if (!E.orthonormalize(cur, e)) break;          // breakdown: the span is invariant
+                copy_block_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.W, b, b, n, E.V + cur, m);
+                if ((rc = E.apply_block(E.V + cur, m, E.AV + cur, m)) != SPMM_OK) break;
+                seed = cur;
+                cur += b;
+            }
+            if (rc != SPMM_OK) break;
+            if (e != cudaSuccess) { fail(e, "spmm_eigs: expand"); break; }
+            // ---- Rayleigh-Ritz on span(V[:, :cur])
+            if ((e = E.tn(E.V, m, cur, E.AV, m, cur, T)) != cudaSuccess) { fail(e, "spmm_eigs: projection"); break; }
+            for (int i = 0; i < cur; ++i)
+                for (int j = i + 1; j < cur; ++j) {
+                    const double a = 0.5 * (T[(size_t)i * cur + j] + T[(size_t)j * cur + i]);
+                    T[(size_t)i * cur + j] = a;
+                    T[(size_t)j * cur + i] = a;
+                }
+            jacobi_eigh(cur, T, th, Y);
+            std::vector<int> order(cur);
+            for (int i = 0; i < cur; ++i) order[i] = i;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return th[x] > th[y]; });
+            const int kp = std::min(keep, cur);
+            std::vector<double> Yk((size_t)cur * kp), thk(kp);
+            for (int c = 0; c < kp; ++c) {
+                thk[c] = th[order[c]];
+                for (int r = 0; r < cur; ++r) Yk[(size_t)r * kp + c] = Y[(size_t)r * cur + order[c]];
+            }
+            if ((e = E.nn(E.V, m, cur, Yk, kp, E.U, kp, 1.0, 0.0)) != cudaSuccess ||
+                (e = E.nn(E.AV, m, cur, Yk, kp, E.AU, kp, 1.0, 0.0)) != cudaSuccess) {
+                fail(e, "spmm_eigs: Ritz vectors");
+                break;
+            }
+            // residual norms of the Ritz pairs
+            cudaMemcpyAsync(E.theta, thk.data(), kp * sizeof(double), cudaMemcpyHostToDevice, E.s);
+            residual_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.AU, E.U, E.theta, kp, n, E.W2);
+            if ((e = E.tn(E.W2, kp, kp, E.W2, kp, kp, Rn)) != cudaSuccess) { fail(e, "spmm_eigs: residuals"); break; }
+            double worst = 0.0;
+            for (int i = 0; i < nev; ++i) worst = std::max(worst, std::sqrt(std::max(0.0, Rn[(size_t)i * kp + i])));
+            if (worst <= tol || restarts >= max_restarts) {
+                for (int i = 0; i < nev; ++i) {
+                    evals[i] = thk[i];
+                    if (resid) resid[i] = std::sqrt(std::max(0.0, Rn[(size_t)i * kp + i]));
+                }
+                if (evecs) copy_block_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.U, kp, nev, n, evecs, nev);
+                if (restarts_out) *restarts_out = restarts;
+                done = true;
+                break;
+            }
+            // ---- thick restart: keep the best kp Ritz vectors and their images
+            copy_block_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.U, kp, kp, n, E.V, m);
+            copy_block_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.AU, kp, kp, n, E.AV, m);
+            cur = kp;
+            seed = 0;
+            ++restarts;
+        }
+        if (rc != SPMM_OK) break;
+        if ((e = cudaStreamSynchronize(E.s)) != cudaSuccess) { fail(e, "spmm_eigs: run"); break; }
+        int32_t st = 0;
+        if ((e = cudaMemcpy(&st, S->status, sizeof(st), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            fail(e, "spmm_eigs: status");
+            break;
+        }
+        if (st != 0) {
+            cudaMemset(S->status, 0, sizeof(int32_t));
+            set_error("spmm_eigs: a device-side staging wait timed out; the result is incomplete");
+            rc = SPMM_ERR_TIMEOUT;
+        }
+    } while (0);
+    if (E.s) {
+        cudaStreamSynchronize(E.s);
+        cudaStreamDestroy(E.s);
+    }
+    cudaFree(E.V); cudaFree(E.AV); cudaFree(E.U); cudaFree(E.AU); cudaFree(E.W); cudaFree(E.W2);
+    cudaFree(E.part); cudaFree(E.small); cudaFree(E.theta); cudaFree(E.Yf); cudaFree(E.Xs);
+    return rc;
+}

@@ -79,6 +79,8 @@ _lib.spmm_create_batched.argtypes = [ctypes.POINTER(_P), _i32, _P, _P, _P, _P, _
 _lib.spmm_create_batched.restype = ctypes.c_int
 _lib.spmm_nmf.argtypes = [_P, _i32, _i32, _P, _P, ctypes.c_int, ctypes.c_double, _P, _P]
 _lib.spmm_nmf.restype = ctypes.c_int
+_lib.spmm_eigs.argtypes = [_P, _i32, _i32, _i32, _i32, ctypes.c_double, ctypes.c_int, _P, _P, _P, _P, _P, _P]
+_lib.spmm_eigs.restype = ctypes.c_int
 _lib.spmm_last_error.argtypes = []
 _lib.spmm_last_error.restype = ctypes.c_char_p
 
@@ -229,6 +231,19 @@ def spmm_nmf(h, k, steps, W, Ht, ftype=SPMM_F32, eps=1e-12, n_graphs=1, stream=N
     return obj
 
 
+def spmm_eigs(h, nev, V0, block=16, max_basis=64, max_restarts=100, tol=1e-6, xtype=SPMM_F32, evecs=None,
+              stream=None):
+    """Top-nev eigenpairs; V0 is a float64 CUDA tensor (n x block).  Returns
+    (evals, residuals, restarts)."""
+    ev = np.zeros(nev, dtype=np.float64)
+    rs = np.zeros(nev, dtype=np.float64)
+    nr = ctypes.c_int32(0)
+    _check(_lib.spmm_eigs(h, int(nev), int(block), int(max_basis), int(max_restarts), float(tol), int(xtype),
+                          _ptr(V0), _P(ev.ctypes.data), _ptr(evecs), _P(rs.ctypes.data), ctypes.byref(nr),
+                          _stream_handle(stream)))
+    return ev, rs, nr.value
+
+
 def spmm_get_info(h) -> dict:
     info = spmm_info()
     _check(_lib.spmm_get_info(h, ctypes.byref(info)))
@@ -256,6 +271,10 @@ class SparseMatrix:
         self.n_cols = int(sum(g.n_cols for g in graphs))
         self.handle = spmm_create_batched(graphs, SPMM_WANT_TRANSPOSE if transpose else 0, opts, stream, weighted)
         return self
+
+    def eigs(self, nev, V0, **kw):
+        """Top-nev eigenpairs of a symmetric matrix: (evals, residuals, restarts)."""
+        return spmm_eigs(self.handle, nev, V0, **kw)
 
     def nmf(self, k, steps, W, Ht, ftype=SPMM_F32, eps=1e-12, stream=None):
         """NMF in place on W (rows x k) and Ht (cols x k); returns objective."""

@@ -196,3 +196,40 @@ def sample_rows(n_rows: int, n: int, seed: int = 0) -> np.ndarray:
     out = np.empty(n, dtype=np.int64)
     _load().synth_sample_rows(seed, n_rows, n, _p(out))
     return out
+
+
+def largest_component(A: CSR) -> CSR:
+    """The largest connected component of a symmetric graph, vertices kept in
+    their original relative order, values carried along (no renormalisation)."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    n = A.n_rows
+    M = csr_matrix((np.ones(A.nnz, dtype=np.int8), A.col_idx, A.row_ptr), shape=(n, n))
+    ncomp, lab = connected_components(M, directed=False)
+    big = np.argmax(np.bincount(lab))
+    keep = np.flatnonzero(lab == big)
+    new_id = np.full(n, -1, dtype=np.int64)
+    new_id[keep] = np.arange(len(keep))
+    deg = np.diff(A.row_ptr)
+    rows = np.repeat(np.arange(n), deg)
+    sel = (new_id[rows] >= 0) & (new_id[A.col_idx] >= 0)
+    r, c = new_id[rows[sel]], new_id[A.col_idx[sel]]
+    row_ptr = np.zeros(len(keep) + 1, dtype=np.int64)
+    np.add.at(row_ptr, r + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    vals = None if A.values is None else A.values[sel].copy()
+    return CSR(len(keep), len(keep), row_ptr, c.astype(np.int32), vals)
+
+
+def sym_rmat_lcc(scale: int, seed: int = 0) -> CSR:
+    """Largest connected component of the symmetrised R-MAT graph with
+    lognormal pair weights, normalised D^-1/2 A D^-1/2 on the component."""
+    A = sym_rmat_csr(scale, seed=seed, normalise=False)
+    L = largest_component(A)
+    # renormalise on the component (its degrees are unchanged: no edge leaves it)
+    deg = np.zeros(L.n_rows)
+    rows = np.repeat(np.arange(L.n_rows), np.diff(L.row_ptr))
+    np.add.at(deg, rows, L.values.astype(np.float64))
+    inv = 1.0 / np.sqrt(deg)
+    L.values = (L.values.astype(np.float64) * inv[rows] * inv[L.col_idx]).astype(np.float32)
+    return L

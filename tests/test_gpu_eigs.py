@@ -1,0 +1,70 @@
+"""GPU block eigensolver (Section 4.2) against closed forms and the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import graphs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sp():
+    from paper_1602_02864_gb300 import spmm
+    return spmm
+
+
+@pytest.fixture(scope="module")
+def lcc12():
+    return synth.sym_rmat_lcc(12, seed=1)
+
+
+def start_block(n, b, seed=0):
+    import torch
+    return torch.from_numpy(synth.dense(n, b, seed=seed).astype(np.float64)).cuda()
+
+
+def test_cycle_closed_form(sp):
+    n = 200
+    i = np.arange(n)
+    C = graphs.csr_from_edges(n, n, np.r_[i, (i + 1) % n], np.r_[(i + 1) % n, i], np.full(2 * n, 0.5))
+    h = sp.SparseMatrix.from_csr(C)
+    ev, res, _ = h.eigs(8, start_block(n, 8), block=8, max_basis=32, max_restarts=400, tol=1e-6)
+    expect = np.sort(np.cos(2 * np.pi * np.arange(n) / n))[::-1][:8]
+    np.testing.assert_allclose(ev, expect, atol=2e-6)
+    assert np.all(res <= 1e-6)
+    h.close()
+
+
+@pytest.mark.parametrize("xdtype,tol,atol", [("f32", 1e-6, 2e-6), ("bf16", 5e-3, 2e-3)])
+def test_rmat_lcc_matches_oracle(sp, lcc12, xdtype, tol, atol):
+    import torch
+    S = lcc12
+    n = S.n_rows
+    h = sp.SparseMatrix.from_csr(S)
+    evecs = torch.zeros((n, 8), dtype=torch.float64, device="cuda")
+    xt = sp.SPMM_F32 if xdtype == "f32" else sp.SPMM_BF16
+    ev, res, nrest = h.eigs(8, start_block(n, 16), block=16, max_basis=64, max_restarts=300, tol=tol, xtype=xt,
+                            evecs=evecs)
+    Q0 = synth.dense(n, 8, seed=9).astype(np.float64)
+    evr, _, _ = oracle.lanczos(n, S.row_ptr, S.col_idx, S.values, Q0, 8, 400)
+    np.testing.assert_allclose(ev, evr, atol=atol)
+    assert np.all(res <= tol), res
+    U = evecs.cpu().numpy()
+    SU = oracle.spmm(n, n, S.row_ptr, S.col_idx, S.values, U)
+    true_res = np.linalg.norm(SU - U * ev[None, :], axis=0)
+    assert np.all(true_res <= 20 * tol), true_res
+    np.testing.assert_allclose(U.T @ U, np.eye(8), atol=1e-8 if xdtype == "f32" else 1e-6)
+    h.close()
+
+
+def test_eigs_argument_errors(sp):
+    n = 100
+    C = graphs.cycle(n)
+    h = sp.SparseMatrix(n, n, C.row_ptr, C.col_idx, None)
+    with pytest.raises(sp.SpmmError):                       # nev + 2*block > max_basis
+        h.eigs(8, start_block(n, 16), block=16, max_basis=32)
+    with pytest.raises(sp.SpmmError):                       # basis larger than n
+        h.eigs(4, start_block(n, 8), block=8, max_basis=200)
+    h.close()

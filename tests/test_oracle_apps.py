@@ -142,3 +142,16 @@ def test_lanczos_vs_dense_eigh_on_rmat():
     Q0 = synth.dense(n, 8, seed=5).astype(np.float64)
     ev, V, m = oracle.lanczos(n, A.row_ptr, A.col_idx, A.values, Q0, 6, n)
     np.testing.assert_allclose(ev, np.sort(np.linalg.eigvalsh(S))[::-1][:6], atol=1e-9)
+
+
+def test_lanczos_vs_dense_eigh_on_normalised_lcc():
+    # the eigensolver's benchmark matrix family: normalised symmetric R-MAT,
+    # largest connected component, top eigenvalue 1 (simple)
+    S = synth.sym_rmat_lcc(9, seed=2)
+    D = graphs.dense_of(S)
+    assert np.allclose(D, D.T)
+    ref = np.sort(np.linalg.eigvalsh(D))[::-1][:8]
+    Q0 = synth.dense(S.n_rows, 8, seed=3).astype(np.float64)
+    ev, V, m = oracle.lanczos(S.n_rows, S.row_ptr, S.col_idx, S.values, Q0, 8, 200)
+    np.testing.assert_allclose(ev, ref, atol=1e-9)
+    assert abs(ev[0] - 1.0) < 1e-9 and ev[1] < 1 - 1e-6

@@ -52,6 +52,7 @@ typedef enum {
 
 /* create flags */
 #define SPMM_WANT_TRANSPOSE 0x1u   /* also build the transposed (CSC) copy for A^T X */
+#define SPMM_HOST_STREAMING 0x2u   /* keep A in host memory and stream it per call (A X only) */
 
 /* Tuning knobs of the warp-task plan (the GPU form of the paper's tile-row
  * batches, Section 3.4); a NULL pointer or a zero field selects the default.
@@ -66,6 +67,11 @@ typedef enum {
  *   x_l2_policy  L2 cache policy of the X gathers: 0 = default
  *              (evict-last), 1 = evict-normal, 2 = evict-last; the
  *              streamed matrix is always read evict-first
+ *   stream_slot_kib  streaming mode: staging slot size for column indices
+ *              in KiB (two slots are used in turn)                 default 262144 (256 MiB)
+ *   debug_fail_block streaming mode, for tests: 1 + the block before
+ *              which the streamer reports an injected copy failure and
+ *              drains (0 = never)
  */
 typedef struct {
     int32_t task_nnz;
@@ -73,7 +79,9 @@ typedef struct {
     int32_t long_row;
     int32_t short_max;
     int32_t x_l2_policy;
-    int32_t reserved[3];
+    int32_t stream_slot_kib;
+    int32_t debug_fail_block;
+    int32_t reserved;
 } spmm_opts;
 
 /* Plan statistics reported by spmm_get_info. */
@@ -104,12 +112,24 @@ typedef struct {
  *   col_idx    nnz int32, 0 <= col < n_cols (any order within a row)
  *   values     nnz values of type vtype, or NULL for a pattern matrix (all 1)
  *   vtype      SPMM_F32, SPMM_BF16 or SPMM_F16 (ignored when values is NULL)
- *   flags      SPMM_WANT_TRANSPOSE or 0
+ *   flags      SPMM_WANT_TRANSPOSE, SPMM_HOST_STREAMING or 0
  *   opts       tuning knobs or NULL
  *   stream     stream for the copies; the call returns after they finish
  * Errors: SPMM_ERR_ARG (null/shape), SPMM_ERR_FORMAT (row_ptr not monotone,
  * wrong row_ptr[0] or row_ptr[n_rows], column out of range), SPMM_ERR_OOM,
- * SPMM_ERR_CUDA.  The input arrays are copied; the caller keeps ownership.
+ * SPMM_ERR_UNSUPPORTED (streaming with SPMM_WANT_TRANSPOSE), SPMM_ERR_CUDA.
+ * The input arrays are copied; the caller keeps ownership.
+ *
+ * Streaming mode (SPMM_HOST_STREAMING; Section 3.1 keeps the sparse matrix
+ * outside memory and streams it while the dense matrices stay resident, and
+ * Section 3.6 argues memory is better spent on the dense side): the matrix is
+ * NOT copied.  The handle borrows row_ptr, col_idx and values, pins them with
+ * cudaHostRegister unless they are already pinned, and every spmm_apply
+ * streams them to HBM in blocks of whole warp tasks through two staging slots
+ * (the copy of one block overlaps the multiplication of the previous one).
+ * The caller must keep the arrays alive and unchanged until spmm_destroy.
+ * Only Y = A X is available; X and Y stay in HBM.  Calls on one streaming
+ * handle share its slots and must not overlap.
  */
 int spmm_create_csr(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, int64_t nnz,
                     const int64_t* row_ptr, const int32_t* col_idx, const void* values,

@@ -20,7 +20,6 @@
 namespace spmm {
 
 static thread_local std::string g_error;
-constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every device-side staging wait (2 s)
 
 void set_error(const std::string& msg) { g_error = msg; }
 
@@ -108,6 +107,8 @@ static Params resolve_params(const spmm_opts* opts) {
         if (opts->short_max > 0) prm.short_max = opts->short_max;
         if (opts->x_l2_policy == 1) prm.x_evict_last = 0;
         if (opts->x_l2_policy == 2) prm.x_evict_last = 1;
+        if (opts->stream_slot_kib > 0) prm.slot_bytes = (int64_t)opts->stream_slot_kib << 10;
+        if (opts->debug_fail_block > 0) prm.fail_block = opts->debug_fail_block;
     }
     prm.task_nnz = std::min(std::max(prm.task_nnz, 32), kMaxTaskNnz);
     prm.task_rows = std::min(std::max(prm.task_rows, 1), kMaxTaskRows);
@@ -179,7 +180,11 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
         return SPMM_ERR_ARG;
     }
     if (!row_ptr || (nnz > 0 && !col_idx)) { set_error(w + ": row_ptr/col_idx is NULL"); return SPMM_ERR_ARG; }
-    if (flags & ~SPMM_WANT_TRANSPOSE) { set_error(w + ": unknown flag bits"); return SPMM_ERR_ARG; }
+    if (flags & ~(SPMM_WANT_TRANSPOSE | SPMM_HOST_STREAMING)) { set_error(w + ": unknown flag bits"); return SPMM_ERR_ARG; }
+    if ((flags & SPMM_HOST_STREAMING) && (flags & SPMM_WANT_TRANSPOSE)) {
+        set_error(w + ": the streaming mode computes A X only (no SPMM_WANT_TRANSPOSE)");
+        return SPMM_ERR_UNSUPPORTED;
+    }
     size_t vsize = 0;
     if (values) {
         if (vtype != SPMM_F32 && vtype != SPMM_BF16 && vtype != SPMM_F16) {
@@ -222,7 +227,24 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
         delete A;
         return cuda_fail(se, (w + ": status word").c_str());
     }
-    int rc = build_orientation(A->fwd, n_rows, n_cols, row_ptr, col_idx, values, vsize, prm, s, &A->device_bytes);
+    int rc;
+    if (flags & SPMM_HOST_STREAMING) {
+        A->streaming = true;
+        A->fwd.n_rows = n_rows;
+        A->fwd.n_cols = n_cols;
+        A->fwd.nnz = nnz;
+        rc = stream_setup(A, row_ptr, col_idx, values, vsize, s);
+        if (rc != SPMM_OK) {
+            stream_release(A);
+            free_dev(A->fwd);
+            cudaFree(A->status);
+            delete A;
+            return rc;
+        }
+        *out = A;
+        return SPMM_OK;
+    }
+    rc = build_orientation(A->fwd, n_rows, n_cols, row_ptr, col_idx, values, vsize, prm, s, &A->device_bytes);
     if (rc == SPMM_OK && (flags & SPMM_WANT_TRANSPOSE)) {
         // CSR of A^T by a stable counting sort on the column index.
         std::vector<int64_t> tptr((size_t)n_cols + 1, 0);
@@ -350,21 +372,10 @@ extern "C" int spmm_create_batched(spmm_mat_t* out, int32_t n_graphs, const int6
 
 namespace spmm {
 
-// Enqueue Y = A X (or A^T X) for a validated handle; shared by spmm_apply and
-// the applications built on it.
-int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
-              int64_t ldy, cudaStream_t s) {
-    const DevCSR& d = transpose ? A->tr : A->fwd;
-    if (d.n_rows == 0) return SPMM_OK;
-    int vmode = 0;
-    if (A->vtype == SPMM_F32) vmode = 1;
-    else if (A->vtype == SPMM_BF16) vmode = 2;
-    else if (A->vtype == SPMM_F16) vmode = 3;
-    if ((vmode == 2 && xtype != SPMM_BF16) || (vmode == 3 && xtype != SPMM_F16)) {
-        set_error("spmm_apply: 16-bit values need X of the same 16-bit type (or use F32 values)");
-        return SPMM_ERR_UNSUPPORTED;
-    }
-    // widest vector that divides k and keeps every X load and Y store aligned
+// Lane geometry of one call: the widest vector that divides k and keeps every
+// X load and Y store aligned, lanes per nonzero and column chunks.
+void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xtype, const float* Y, int64_t ldy,
+                  int* vec_out, int* ch_out) {
     const int esize = (int)dtype_size(xtype);
     const uintptr_t xa = (uintptr_t)X, ya = (uintptr_t)Y;
     int vec = 16 / esize;
@@ -379,8 +390,47 @@ int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int3
     const int per = (nvec + ch - 1) / ch;
     int lg = 0;
     while ((1 << lg) < per) ++lg;
+    a.X = X;
+    a.ldx = ldx;
+    a.Y = const_cast<float*>(Y);
+    a.ldy = ldy;
+    a.k = k;
+    a.lanes_log2 = lg;
+    a.nvec = nvec;
+    *vec_out = vec;
+    *ch_out = ch;
+}
 
+int value_mode(const spmm_mat* A, int32_t xtype) {
+    int vmode = 0;
+    if (A->vtype == SPMM_F32) vmode = 1;
+    else if (A->vtype == SPMM_BF16) vmode = 2;
+    else if (A->vtype == SPMM_F16) vmode = 3;
+    if ((vmode == 2 && xtype != SPMM_BF16) || (vmode == 3 && xtype != SPMM_F16)) return -1;
+    return vmode;
+}
+
+cudaError_t launch_rows(const FwdArgs& a, int32_t xtype, int vmode, int vec, int ch, cudaStream_t s) {
+    if (xtype == SPMM_F32) return launch_rows_f32(a, vmode, vec, ch, s);
+    if (xtype == SPMM_BF16) return launch_rows_bf16(a, vmode, vec, ch, s);
+    return launch_rows_f16(a, vmode, vec, ch, s);
+}
+
+// Enqueue Y = A X (or A^T X) for a validated handle; shared by spmm_apply and
+// the applications built on it.
+int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
+              int64_t ldy, cudaStream_t s) {
+    if (A->streaming && !transpose) return stream_apply(A, X, ldx, k, xtype, Y, ldy, s);
+    const DevCSR& d = transpose ? A->tr : A->fwd;
+    if (d.n_rows == 0) return SPMM_OK;
+    const int vmode = value_mode(A, xtype);
+    if (vmode < 0) {
+        set_error("spmm_apply: 16-bit values need X of the same 16-bit type (or use F32 values)");
+        return SPMM_ERR_UNSUPPORTED;
+    }
     FwdArgs a;
+    int vec = 1, ch = 1;
+    set_geometry(a, X, ldx, k, xtype, Y, ldy, &vec, &ch);
     a.row_ptr = d.row_ptr;
     a.col_idx = d.col_idx;
     a.val = d.val;
@@ -390,17 +440,7 @@ int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int3
     a.status = A->status;
     a.wait_ns = kWaitNs;
     a.x_evict_last = A->params.x_evict_last;
-    a.X = X;
-    a.ldx = ldx;
-    a.Y = Y;
-    a.ldy = ldy;
-    a.k = k;
-    a.lanes_log2 = lg;
-    a.nvec = nvec;
-    cudaError_t e;
-    if (xtype == SPMM_F32) e = launch_rows_f32(a, vmode, vec, ch, s);
-    else if (xtype == SPMM_BF16) e = launch_rows_bf16(a, vmode, vec, ch, s);
-    else e = launch_rows_f16(a, vmode, vec, ch, s);
+    cudaError_t e = launch_rows(a, xtype, vmode, vec, ch, s);
     if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: task kernel");
     e = launch_combine(d.splits, d.n_splits, d.partials, Y, ldy, k, s);
     if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: combine kernel");
@@ -453,6 +493,7 @@ extern "C" int spmm_get_info(spmm_mat_t A, spmm_info* info) {
 extern "C" int spmm_destroy(spmm_mat_t A) {
     if (!A) return SPMM_OK;
     cudaError_t e = cudaDeviceSynchronize();
+    if (A->streaming) stream_release(A);
     free_dev(A->fwd);
     free_dev(A->tr);
     cudaFree(A->status);

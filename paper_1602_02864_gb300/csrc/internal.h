@@ -25,6 +25,7 @@ constexpr int kMaxTaskNnz = 512;    // staged nonzeros per task (shared memory)
 constexpr int kMaxTaskRows = 64;    // rows per short-row task
 constexpr int kSlotStride = 64;     // floats per partial-result slot (k <= 64)
 constexpr int kMaxK = 64;
+constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every device-side staging wait (2 s)
 // per-warp staging buffer (one of two): column indices, values, row pointers,
 // each padded for 16-byte aligned bulk copies of an unaligned window
 constexpr int kColBufInts = kMaxTaskNnz + 8;          // 2080 bytes
@@ -54,12 +55,38 @@ struct DevCSR {
     int64_t n_slots = 0;
 };
 
+// Streaming mode: the matrix stays in (pinned) host memory and flows to HBM
+// in blocks of whole tasks, two staging slots used in turn.
+struct StreamBlock {
+    int64_t t0, t1;     // task range
+    int64_t c0, c1;     // column-index / value range copied (c0 aligned down to 8)
+    int64_t r0, r1;     // row-pointer range copied (r0 aligned down to 2)
+};
+
+struct Streamer {
+    const int64_t* h_row_ptr = nullptr;
+    const int32_t* h_col_idx = nullptr;
+    const void* h_val = nullptr;
+    bool reg_rp = false, reg_ci = false, reg_val = false;   // registered by the library
+    std::vector<StreamBlock> blocks;
+    int32_t* slot_col[2] = {nullptr, nullptr};
+    void* slot_val[2] = {nullptr, nullptr};
+    int64_t* slot_rp[2] = {nullptr, nullptr};
+    int64_t slot_nnz = 0, slot_rows = 0;   // capacities
+    cudaStream_t copy = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+    int32_t fail_block = 0;                // test hook: 1 + block before which a copy "fails"
+    int64_t bytes_per_apply = 0;           // host bytes streamed per call
+};
+
 struct Params {
     int32_t task_nnz = 256;     // nonzeros per short-row task
     int32_t task_rows = 64;     // rows per short-row task
     int32_t long_row = 512;     // rows longer than this are split
     int32_t short_max = 31;     // rows with more nonzeros are "long"
     int32_t x_evict_last = 1;   // L2 policy of the X gathers (1 = evict-last)
+    int64_t slot_bytes = 256ll << 20;   // streaming staging slot (column indices)
+    int32_t fail_block = 0;
 };
 
 }  // namespace spmm
@@ -76,6 +103,8 @@ struct spmm_mat {
     // row_off[g] .. row_off[g+1]-1 and columns col_off[g] .. col_off[g+1]-1
     std::vector<int64_t> row_off, col_off;
     std::vector<double> a2;     // ||A_g||_F^2 per graph
+    bool streaming = false;
+    spmm::Streamer st;
 };
 
 namespace spmm {
@@ -88,6 +117,18 @@ void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
               int64_t ldy, cudaStream_t s);
+struct FwdArgs;
+void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xtype, const float* Y, int64_t ldy,
+                  int* vec_out, int* ch_out);
+int value_mode(const spmm_mat* A, int32_t xtype);
+cudaError_t launch_rows(const FwdArgs& a, int32_t xtype, int vmode, int vec, int ch, cudaStream_t s);
+
+// stream.cu
+int stream_setup(spmm_mat* A, const int64_t* row_ptr, const int32_t* col_idx, const void* values, size_t vsize,
+                 cudaStream_t s);
+int stream_apply(const spmm_mat* A, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y, int64_t ldy,
+                 cudaStream_t s);
+void stream_release(spmm_mat* A);
 
 // Arguments of the task kernel (one instantiation per x type / value type /
 // vector width / column chunks).

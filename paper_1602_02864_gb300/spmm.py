@@ -22,6 +22,7 @@ SPMM_OK = 0
 SPMM_ERR_ARG, SPMM_ERR_CUDA, SPMM_ERR_OOM, SPMM_ERR_FORMAT, SPMM_ERR_TIMEOUT, SPMM_ERR_UNSUPPORTED = (
     -1, -2, -3, -4, -5, -6)
 SPMM_WANT_TRANSPOSE = 0x1
+SPMM_HOST_STREAMING = 0x2
 
 _STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_FORMAT", -5: "ERR_TIMEOUT",
            -6: "ERR_UNSUPPORTED"}
@@ -35,7 +36,8 @@ class SpmmError(RuntimeError):
 
 class spmm_opts(ctypes.Structure):
     _fields_ = [("task_nnz", ctypes.c_int32), ("task_rows", ctypes.c_int32), ("long_row", ctypes.c_int32),
-                ("short_max", ctypes.c_int32), ("x_l2_policy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("short_max", ctypes.c_int32), ("x_l2_policy", ctypes.c_int32), ("stream_slot_kib", ctypes.c_int32),
+                ("debug_fail_block", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class spmm_info(ctypes.Structure):
@@ -258,10 +260,16 @@ class SparseMatrix:
     """A sparse matrix resident in HBM: ``SparseMatrix(A_csr).apply(X)``."""
 
     def __init__(self, n_rows, n_cols, row_ptr, col_idx, values=None, transpose=False,
-                 opts: spmm_opts | None = None, stream=None):
+                 opts: spmm_opts | None = None, stream=None, streaming=False):
         self.n_rows, self.n_cols = int(n_rows), int(n_cols)
-        self.handle = spmm_create_csr(n_rows, n_cols, row_ptr, col_idx, values,
-                                      SPMM_WANT_TRANSPOSE if transpose else 0, opts, stream)
+        flags = (SPMM_WANT_TRANSPOSE if transpose else 0) | (SPMM_HOST_STREAMING if streaming else 0)
+        if streaming:
+            # the library borrows these host arrays until close(): keep them alive
+            self._borrowed = (np.ascontiguousarray(row_ptr, dtype=np.int64),
+                              np.ascontiguousarray(col_idx, dtype=np.int32),
+                              None if values is None else np.ascontiguousarray(values))
+            row_ptr, col_idx, values = self._borrowed
+        self.handle = spmm_create_csr(n_rows, n_cols, row_ptr, col_idx, values, flags, opts, stream)
 
     @classmethod
     def batched(cls, graphs, transpose=False, weighted=True, opts: spmm_opts | None = None, stream=None):

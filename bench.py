@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--pagerank-iters", type=int, default=30)
+    ap.add_argument("--workload", default="ksweep", choices=["ksweep", "streaming", "nmf-batched", "eigs"],
+                    help="ksweep: the headline SpMM sweep + PageRank; the others measure the streaming mode, "
+                         "the batched launch with NMF and the eigensolver")
     return ap.parse_args()
 
 
@@ -199,6 +202,195 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def event_ms(fn, reps, flush=None):
+    """Mean CUDA-event time of fn() on the current stream (L2 flushed first)."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.mean(ts)
+
+
+def base_line(args, metric, value, unit, ms, workload, dtype, extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": {"workload": workload}}
+    line.update(extra)
+    return line
+
+
+def workload_streaming(args):
+    """Streaming mode: A (R-MAT, avg degree 32) in pinned host memory, X and Y
+    (k = 4, FP32) in HBM; link bytes per call vs the measured pinned H2D peak."""
+    import torch
+    import oracle
+    from paper_1602_02864_gb300 import spmm
+    scale = args.scale if args.scale != 24 else 26
+    t = time.time()
+    A = synth.rmat_csr(scale, 32 << scale, seed=0)
+    t_gen = time.time() - t
+    N, nnz = A.n_rows, A.nnz
+    # pinned host -> device peak: large copies, best of 5
+    buf = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    dbuf = torch.empty_like(buf, device="cuda")
+    peak = max((1 << 30) / (event_ms(lambda: dbuf.copy_(buf, non_blocking=True), 1) / 1e3) / 1e9 for _ in range(5))
+    del buf, dbuf
+    t = time.time()
+    h = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, streaming=True)
+    t_create = time.time() - t
+    k = 4
+    X = torch.from_numpy(synth.dense(N, k, seed=0)).cuda()
+    Y = torch.empty((N, k), device="cuda")
+    for _ in range(args.warmup):
+        h.apply(X, Y=Y)
+    ms = event_ms(lambda: h.apply(X, Y=Y), args.steps)
+    link_bytes = nnz * 4 + (N + 1) * 8
+    # resident mode on the same matrix for context
+    hr = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None)
+    Yr = torch.empty_like(Y)
+    for _ in range(2):
+        hr.apply(X, Y=Yr)
+    ms_res = event_ms(lambda: hr.apply(X, Y=Yr), args.steps)
+    same = bool(torch.equal(Y, Yr))
+    hr.close()
+    rows = np.unique(synth.sample_rows(N, 100_000, seed=5))
+    Xh = X.cpu().numpy()
+    ref = oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xh, rows, threads=oracle.num_threads())
+    scale_ = oracle.spmm_rows(A.row_ptr, A.col_idx, None, np.abs(Xh), rows, threads=oracle.num_threads())
+    got = Y[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    err = float((np.abs(got - ref) / np.maximum(scale_, 1e-300)).max())
+    h.sync_status()
+    h.close()
+    achieved = link_bytes / (ms / 1e3) / 1e9
+    return base_line(args, f"streaming SpMM nonzeros/s (R-MAT scale {scale}, avg degree 32, k=4, A in host memory)",
+                     nnz / (ms / 1e3), "nnz/s", ms, f"rmat{scale}-streaming-k4", "f32",
+                     {"link": {"achieved_GBps": achieved, "peak_pinned_h2d_GBps": peak, "frac": achieved / peak,
+                               "bytes_per_call": link_bytes},
+                      "resident_ms": ms_res, "bit_identical_to_resident": same,
+                      "sampled_rows_max_err_over_absprod": err, "sampled_rows": int(len(rows)),
+                      "n": N, "nnz": nnz, "setup_s": {"generate": round(t_gen, 1), "create": round(t_create, 1)}})
+
+
+def workload_nmf_batched(args):
+    """256 Chung-Lu graphs in one block-diagonal handle: batched SpMM vs one
+    launch per graph, then NMF (k = 8, 16, 32; 50 steps; FP32 and BF16)."""
+    import torch
+    import oracle
+    from paper_1602_02864_gb300 import spmm
+    n_graphs = 256
+    graphs = [synth.chunglu_csr(g, seed=0) for g in range(n_graphs)]
+    nnz = sum(g.nnz for g in graphs)
+    nv = sum(g.n_rows for g in graphs)
+    h = spmm.SparseMatrix.batched(graphs, transpose=True, weighted=False)
+    singles = [spmm.SparseMatrix(g.n_rows, g.n_cols, g.row_ptr, g.col_idx, None) for g in graphs]
+    k = 16
+    Xs = [torch.from_numpy(synth.dense(g.n_cols, k, seed=i)).cuda() for i, g in enumerate(graphs)]
+    Xb = torch.cat(Xs)
+    Ys = [torch.empty((g.n_rows, k), device="cuda") for g in graphs]
+    Yb = torch.empty((nv, k), device="cuda")
+    for _ in range(args.warmup):
+        h.apply(Xb, Y=Yb)
+        for s_, x, y in zip(singles, Xs, Ys):
+            s_.apply(x, Y=y)
+    ms_b = event_ms(lambda: h.apply(Xb, Y=Yb), args.steps)
+
+    def per_graph():
+        for s_, x, y in zip(singles, Xs, Ys):
+            s_.apply(x, Y=y)
+    ms_p = event_ms(per_graph, args.steps)
+    same = all(torch.equal(Yb[o:o + g.n_rows], y) for o, g, y in
+               zip(np.cumsum([0] + [g.n_rows for g in graphs[:-1]]), graphs, Ys))
+    for s_ in singles:
+        s_.close()
+    nmf = {}
+    steps = 50
+    for kk in (8, 16, 32):
+        for ft, name in ((spmm.SPMM_F32, "f32"), (spmm.SPMM_BF16, "bf16")):
+            W0 = torch.from_numpy(np.concatenate([synth.dense(g.n_rows, kk, seed=1000 + i, mode="unit") + 0.01
+                                                  for i, g in enumerate(graphs)])).cuda()
+            H0 = torch.from_numpy(np.concatenate([synth.dense(g.n_cols, kk, seed=2000 + i, mode="unit") + 0.01
+                                                  for i, g in enumerate(graphs)])).cuda()
+            W, H = W0.clone(), H0.clone()
+            t0 = time.perf_counter()
+            obj = h.nmf(kk, steps, W, H, ftype=ft)
+            dt = time.perf_counter() - t0
+            nmf[f"k{kk}_{name}"] = {"ms_per_call": round(dt * 1e3, 2), "ms_per_step": round(dt * 1e3 / steps, 3),
+                                    "spmm_nnz_per_s": 2 * nnz * steps / dt,
+                                    "objective_ratio_last_over_first_median":
+                                        float(np.median(obj[:, -1] / obj[:, 0])),
+                                    "monotone_graphs": int(np.sum(np.all(np.diff(obj, axis=1)
+                                                                         <= 1e-5 * obj[:, :-1], axis=1)))}
+            if kk == 16 and name == "f32":
+                # parity on the 4 smallest graphs against the FP64 oracle
+                offs_r = np.cumsum([0] + [g.n_rows for g in graphs])
+                offs_c = np.cumsum([0] + [g.n_cols for g in graphs])
+                w0, h0 = W0.cpu().numpy(), H0.cpu().numpy()
+                worst = 0.0
+                for i in np.argsort([g.n_rows for g in graphs])[:4]:
+                    g = graphs[i]
+                    _, _, objr = oracle.nmf(g.n_rows, g.n_cols, g.row_ptr, g.col_idx, None,
+                                            w0[offs_r[i]:offs_r[i + 1]], h0[offs_c[i]:offs_c[i + 1]], steps)
+                    worst = max(worst, float(np.max(np.abs(obj[i] - objr) / objr)))
+                nmf[f"k{kk}_{name}"]["oracle_objective_max_rel_err_4_smallest"] = worst
+    h.close()
+    return base_line(args, "batched SpMM nonzeros/s (256 Chung-Lu graphs, one launch, k=16, FP32)",
+                     nnz / (ms_b / 1e3), "nnz/s", ms_b, "chunglu256-batched-k16", "f32",
+                     {"per_graph_launches_ms": ms_p, "batched_speedup": ms_p / ms_b, "bit_identical": same,
+                      "graphs": n_graphs, "vertices": nv, "nnz": nnz, "nmf_50_steps": nmf})
+
+
+def workload_eigs(args):
+    """Top 8 eigenpairs of the normalised symmetrised R-MAT graph (largest
+    component), block 16: FP32 vs BF16 SpMM inputs; errors vs the FP64 oracle
+    at scale 18."""
+    import torch
+    import oracle
+    from paper_1602_02864_gb300 import spmm
+    out = {}
+    for scale in (18, args.scale if args.scale != 24 else 25):
+        t = time.time()
+        S = synth.sym_rmat_lcc(scale, seed=0)
+        t_gen = time.time() - t
+        n = S.n_rows
+        h = spmm.SparseMatrix.from_csr(S)
+        V0 = torch.from_numpy(synth.dense(n, 16, seed=1).astype(np.float64)).cuda()
+        X = torch.from_numpy(synth.dense(n, 16, seed=2)).cuda()
+        Y = torch.empty((n, 16), device="cuda")
+        flush = torch.empty(512 << 18, device="cuda")
+        ms32 = event_ms(lambda: h.apply(X, Y=Y), args.steps, flush)
+        xb = X.to(torch.bfloat16)
+        ms16 = event_ms(lambda: h.apply(xb, Y=Y), args.steps, flush)
+        res = {"n": n, "nnz": S.nnz, "spmm_k16_ms_f32": ms32, "spmm_k16_ms_bf16": ms16,
+               "bf16_spmm_speedup": ms32 / ms16, "generate_s": round(t_gen, 1)}
+        ref = None
+        if scale == 18:
+            Q0 = synth.dense(n, 8, seed=9).astype(np.float64)
+            # a plain Lanczos needs a large basis on this clustered spectrum (240 was not enough)
+            ref, _, _ = oracle.lanczos(n, S.row_ptr, S.col_idx, S.values, Q0, 8, 520)
+        for xt, name, tol in ((spmm.SPMM_F32, "f32", 1e-6 if scale <= 20 else 1e-5), (spmm.SPMM_BF16, "bf16", 5e-3)):
+            t0 = time.perf_counter()
+            ev, rs, nrest = h.eigs(8, V0, block=16, max_basis=64, max_restarts=300, tol=tol, xtype=xt)
+            dt = time.perf_counter() - t0
+            r = {"s": round(dt, 2), "restarts": nrest, "evals": ev.tolist(), "max_residual": float(rs.max())}
+            if ref is not None:
+                r["max_rel_err_vs_fp64_oracle"] = float(np.max(np.abs(ev - ref) / np.abs(ref)))
+            res[name] = r
+        h.close()
+        out[f"scale{scale}"] = res
+        del S
+    big = out[max(out)]
+    return base_line(args, "eigensolver SpMM (k=16) nonzeros/s, BF16 X (R-MAT LCC, normalised)",
+                     big["nnz"] / (big["spmm_k16_ms_bf16"] / 1e3), "nnz/s", big["spmm_k16_ms_bf16"],
+                     "symrmat-lcc-eigs-top8-block16", "bf16", {"results": out})
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -206,6 +398,12 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.workload != "ksweep":
+        import torch
+        torch.cuda.set_device(local)
+        fn = {"streaming": workload_streaming, "nmf-batched": workload_nmf_batched, "eigs": workload_eigs}
+        print(json.dumps(fn[args.workload](args)), flush=True)
+        return
 
     import torch
     import torch.distributed as dist

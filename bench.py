@@ -426,6 +426,20 @@ def main():
     h = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, transpose=args.pagerank_iters > 0)
     torch.cuda.synchronize()
     t_create = time.time() - t0
+    # autotune the plan of each orientation on a short candidate list
+    t0 = time.time()
+    cands = [dict(task_nnz=512, short_max=63, long_row=512, x_l2_policy=2),
+             dict(task_nnz=512, short_max=31, long_row=512, x_l2_policy=2),
+             dict(task_nnz=256, short_max=63, long_row=512, x_l2_policy=2),
+             dict(task_nnz=512, short_max=63, long_row=512, x_l2_policy=1)]
+    tuned = {}
+    kt = 8 if 8 in ks else ks[0]
+    best, times, _ = spmm.spmm_autotune(h.handle, kt, spmm.SPMM_F32, 0, cands, reps=2)
+    tuned["forward"] = dict(cands[best], k=kt, ms=round(float(times[best]), 4))
+    if args.pagerank_iters:
+        best, times, _ = spmm.spmm_autotune(h.handle, 1, spmm.SPMM_F32, 1, cands, reps=2)
+        tuned["transpose"] = dict(cands[best], k=1, ms=round(float(times[best]), 4))
+    t_tune = time.time() - t0
     info = h.info()
     kmax = max(ks)
     Xh = synth.dense(N, kmax, seed=0)
@@ -621,7 +635,8 @@ def main():
             "clocks": clk.summary(),
             "gpu_launches": (launches_per_apply * len(ks) + launches_per_pr_iter * args.pagerank_iters
                              + (4 if args.pagerank_iters else 0)) * args.steps,
-            "setup_s": {"generate": round(t_gen, 2), "create": round(t_create, 2)},
+            "setup_s": {"generate": round(t_gen, 2), "create": round(t_create, 2), "autotune": round(t_tune, 2)},
+            "autotuned_plan": tuned,
             "plan": {"tasks": info["n_tasks"], "split_rows": info["n_split_rows"], "segments": info["n_segments"]},
         }
         print(json.dumps(line), flush=True)

@@ -57,13 +57,13 @@ typedef enum {
 /* Tuning knobs of the warp-task plan (the GPU form of the paper's tile-row
  * batches, Section 3.4); a NULL pointer or a zero field selects the default.
  *   task_nnz   nonzeros per task of short rows; segment length of split
- *              rows                                            default 256, 32..512
+ *              rows                                            default 512, 32..512
  *   task_rows  rows per task of short rows                     default 64, 1..64
  *   long_row   rows with more nonzeros are split into segments
  *              combined in a fixed order (deterministic)       default 512, task_nnz..512
  *   short_max  rows with at most this many nonzeros are "short"
  *              (one lane group per row); longer rows get a
- *              whole warp                                      default 31, < task_nnz
+ *              whole warp                                      default 63, < task_nnz
  *   x_l2_policy  L2 cache policy of the X gathers: 0 = default
  *              (evict-last), 1 = evict-normal, 2 = evict-last; the
  *              streamed matrix is always read evict-first
@@ -325,6 +325,33 @@ int spmm_nmf(spmm_mat_t A, int32_t k, int32_t steps, float* W, float* Ht, spmm_d
 int spmm_eigs(spmm_mat_t S, int32_t nev, int32_t block, int32_t max_basis, int32_t max_restarts, double tol,
               spmm_dtype xtype, const double* V0, double* evals, double* evecs, double* resid,
               int32_t* restarts_out, void* stream);
+
+/*
+ * spmm_replan -- rebuild the warp-task plan of one orientation of a resident
+ * handle for new tuning knobs (the matrix itself is not copied again).  The
+ * paper sizes its tile-row batches from the cache size and the number of
+ * dense columns (Section 3.4); here the batch shape is tunable per call site.
+ *   opts        new knobs (NULL = defaults); transpose selects the A^T plan
+ * Synchronises `stream`.  Errors: SPMM_ERR_ARG, SPMM_ERR_UNSUPPORTED
+ * (streaming handles), SPMM_ERR_OOM, SPMM_ERR_CUDA.
+ */
+int spmm_replan(spmm_mat_t A, const spmm_opts* opts, int32_t transpose, void* stream);
+
+/*
+ * spmm_autotune -- time Y = A X (or A^T X) under candidate plans and leave
+ * the handle on the fastest.  Each candidate is planned with spmm_replan,
+ * warmed twice and timed `reps` times with CUDA events, L2 flushed before
+ * every timed call.  X is filled inside with a fixed pattern of type xtype.
+ *   candidates    caller's candidate knobs, or NULL for the built-in grid:
+ *                 task_nnz {128,256,512} x short_max {7,15,31,63} x
+ *                 x_l2_policy {1,2} (long_row 512), 24 candidates
+ *   n_candidates  number of caller candidates (ignored when NULL)
+ *   best_index    out: index of the fastest candidate
+ *   times_ms      host double[number of candidates] or NULL: mean ms each
+ * Synchronises `stream`; allocates its workspace.  Errors as spmm_replan.
+ */
+int spmm_autotune(spmm_mat_t A, int32_t k, spmm_dtype xtype, int32_t transpose, const spmm_opts* candidates,
+                  int32_t n_candidates, int32_t reps, int32_t* best_index, double* times_ms, void* stream);
 
 /* spmm_get_info -- plan statistics of a handle (host call, no GPU work). */
 int spmm_get_info(spmm_mat_t A, spmm_info* info);

@@ -1,0 +1,61 @@
+"""Autotuned plans with a JSON cache.
+
+spmm_autotune (in the library) times candidate warp-task plans for one call
+shape and leaves the handle on the fastest.  This module remembers the
+winner per (GPU, matrix shape and nonzeros, value type, k, X type,
+orientation) in a JSON file, so a later process re-plans directly instead of
+searching again.
+"""
+from __future__ import annotations
+
+import json
+import os
+import tempfile
+
+from . import spmm as _sp
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "spmm_autotune.json")
+
+
+def _key(h, k, xtype, transpose) -> str:
+    import torch
+    info = _sp.spmm_get_info(h)
+    return "|".join(str(x) for x in (torch.cuda.get_device_name(), info["n_rows"], info["n_cols"], info["nnz"],
+                                     info["value_dtype"], k, xtype, int(bool(transpose))))
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(path, data):
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    fd, tmp = tempfile.mkstemp(dir=os.path.dirname(path) or ".", suffix=".tmp")
+    with os.fdopen(fd, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tune(matrix, k, xtype=_sp.SPMM_F32, transpose=False, cache_path: str | None = DEFAULT_CACHE, candidates=None,
+         reps=3) -> dict:
+    """Put `matrix` (a SparseMatrix) on the best plan for this call shape.
+    Returns the chosen knobs (with "ms" and "cached")."""
+    h = matrix.handle
+    key = _key(h, k, xtype, transpose)
+    cache = _load(cache_path) if cache_path else {}
+    if key in cache:
+        knobs = {n: v for n, v in cache[key].items() if n in ("task_nnz", "task_rows", "long_row", "short_max",
+                                                                "x_l2_policy")}
+        _sp.spmm_replan(h, _sp.spmm_opts(**knobs), int(transpose))
+        return dict(cache[key], cached=True)
+    best, times, cands = _sp.spmm_autotune(h, k, xtype, int(transpose), candidates, reps)
+    choice = dict(cands[best], ms=float(times[best]))
+    if cache_path:
+        cache = _load(cache_path)
+        cache[key] = choice
+        _save(cache_path, cache)
+    return dict(choice, cached=False)

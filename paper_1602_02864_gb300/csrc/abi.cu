@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -536,4 +537,156 @@ extern "C" int spmm_debug_wait_timeout(uint64_t wait_ns, void* stream) {
         return SPMM_ERR_TIMEOUT;
     }
     return SPMM_OK;
+}
+
+// ------------------------------------------------------------------ re-planning and autotuning
+namespace spmm {
+
+// Rebuild the task plan of one orientation for new parameters; the matrix
+// itself stays where it is.
+static int replan_orientation(DevCSR& d, const Params& p, cudaStream_t s, int64_t* bytes) {
+    std::vector<int64_t> rp;
+    try {
+        rp.resize((size_t)d.n_rows + 1);
+    } catch (const std::bad_alloc&) {
+        set_error("replan: out of host memory");
+        return SPMM_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpyAsync(rp.data(), d.row_ptr, rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "replan: row pointers");
+    HostPlan plan = build_plan(rp.data(), d.n_rows, p);
+    int4 *tasks = nullptr, *splits = nullptr;
+    float* partials = nullptr;
+    int64_t added = 0;
+    if ((e = upload(&tasks, plan.tasks.data(), plan.tasks.size(), 0, s, &added)) != cudaSuccess ||
+        (e = upload(&splits, plan.splits.data(), plan.splits.size(), 0, s, &added)) != cudaSuccess ||
+        (plan.n_slots > 0 &&
+         (e = cudaMalloc((void**)&partials, (size_t)plan.n_slots * kSlotStride * sizeof(float))) != cudaSuccess)) {
+        cudaFree(tasks);
+        cudaFree(splits);
+        return cuda_fail(e, "replan: upload");
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "replan: sync");
+    *bytes -= (int64_t)((d.n_tasks + 1) * sizeof(int4) + d.n_splits * sizeof(int4) +
+                        d.n_slots * kSlotStride * sizeof(float));
+    *bytes += added + (int64_t)(plan.n_slots * kSlotStride * sizeof(float));
+    cudaFree(d.tasks);
+    cudaFree(d.splits);
+    cudaFree(d.partials);
+    d.tasks = tasks;
+    d.n_tasks = (int64_t)plan.tasks.size() - 1;
+    d.splits = splits;
+    d.n_splits = (int64_t)plan.splits.size();
+    d.n_segments = plan.n_segments;
+    d.partials = partials;
+    d.n_slots = plan.n_slots;
+    return SPMM_OK;
+}
+
+__global__ void fill_x_kernel(void* X, int64_t n, int xtype) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = (float)((i * 2654435761ull) % 1000ull) * 1e-3f - 0.5f;
+        if (xtype == SPMM_F32) static_cast<float*>(X)[i] = v;
+        else if (xtype == SPMM_BF16) static_cast<__nv_bfloat16*>(X)[i] = __float2bfloat16(v);
+        else static_cast<__half*>(X)[i] = __float2half(v);
+    }
+}
+
+}  // namespace spmm
+
+extern "C" int spmm_replan(spmm_mat_t A, const spmm_opts* opts, int32_t transpose, void* stream) {
+    if (!A) { set_error("spmm_replan: A is NULL"); return SPMM_ERR_ARG; }
+    if (A->streaming) { set_error("spmm_replan: not available for streaming handles"); return SPMM_ERR_UNSUPPORTED; }
+    if (transpose && !A->has_tr) { set_error("spmm_replan: no transposed copy"); return SPMM_ERR_ARG; }
+    const Params p = resolve_params(opts);
+    const int rc = replan_orientation(transpose ? A->tr : A->fwd, p, (cudaStream_t)stream, &A->device_bytes);
+    if (rc == SPMM_OK) {
+        // the L2 policy is a launch parameter shared by both orientations
+        A->params.x_evict_last = p.x_evict_last;
+        if (!transpose) A->params = p;
+    }
+    return rc;
+}
+
+extern "C" int spmm_autotune(spmm_mat_t A, int32_t k, spmm_dtype xtype, int32_t transpose,
+                             const spmm_opts* candidates, int32_t n_candidates, int32_t reps, int32_t* best_index,
+                             double* times_ms, void* stream) {
+    if (!A || !best_index) { set_error("spmm_autotune: NULL argument"); return SPMM_ERR_ARG; }
+    if (k < 1 || k > kMaxK || reps < 1 || (candidates && n_candidates < 1)) {
+        set_error("spmm_autotune: need 1 <= k <= 64, reps >= 1, n_candidates >= 1");
+        return SPMM_ERR_ARG;
+    }
+    if (xtype != SPMM_F32 && xtype != SPMM_BF16 && xtype != SPMM_F16) {
+        set_error("spmm_autotune: X must be F32, BF16 or F16");
+        return SPMM_ERR_ARG;
+    }
+    if (A->streaming) { set_error("spmm_autotune: not available for streaming handles"); return SPMM_ERR_UNSUPPORTED; }
+    if (transpose && !A->has_tr) { set_error("spmm_autotune: no transposed copy"); return SPMM_ERR_ARG; }
+    // built-in search space: task size x short-row limit x L2 policy of X
+    std::vector<spmm_opts> grid;
+    if (candidates) {
+        grid.assign(candidates, candidates + n_candidates);
+    } else {
+        for (int tn : {128, 256, 512})
+            for (int sm : {7, 15, 31, 63})
+                for (int pol : {1, 2}) {
+                    if (sm >= tn) continue;
+                    spmm_opts o{};
+                    o.task_nnz = tn;
+                    o.short_max = sm;
+                    o.long_row = 512;
+                    o.x_l2_policy = pol;
+                    grid.push_back(o);
+                }
+    }
+    const DevCSR& d = transpose ? A->tr : A->fwd;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t esz = xtype == SPMM_F32 ? 4 : 2;
+    void* X = nullptr;
+    float* Y = nullptr;
+    void* flush = nullptr;
+    const size_t flush_bytes = 256u << 20;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = SPMM_OK;
+    cudaError_t e;
+    if ((e = cudaMalloc(&X, (size_t)std::max<int64_t>(d.n_cols, 1) * k * esz)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&Y, (size_t)std::max<int64_t>(d.n_rows, 1) * k * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&flush, flush_bytes)) != cudaSuccess || (e = cudaEventCreate(&e0)) != cudaSuccess ||
+        (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        rc = cuda_fail(e, "spmm_autotune: workspace");
+    }
+    int best = -1;
+    double best_ms = 0.0;
+    if (rc == SPMM_OK) {
+        fill_x_kernel<<<1024, 256, 0, s>>>(X, d.n_cols * k, xtype);
+        for (size_t c = 0; c < grid.size() && rc == SPMM_OK; ++c) {
+            if ((rc = spmm_replan(A, &grid[c], transpose, stream)) != SPMM_OK) break;
+            for (int w = 0; w < 2 && rc == SPMM_OK; ++w) rc = apply_dev(A, transpose, X, k, k, xtype, Y, k, s);
+            double total = 0.0;
+            for (int r = 0; r < reps && rc == SPMM_OK; ++r) {
+                cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);   // evict the previous call from L2
+                cudaEventRecord(e0, s);
+                rc = apply_dev(A, transpose, X, k, k, xtype, Y, k, s);
+                cudaEventRecord(e1, s);
+                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { rc = cuda_fail(e, "spmm_autotune: timing"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                total += ms;
+            }
+            if (rc != SPMM_OK) break;
+            const double mean = total / reps;
+            if (times_ms) times_ms[c] = mean;
+            if (best < 0 || mean < best_ms) { best = (int)c; best_ms = mean; }
+        }
+        if (rc == SPMM_OK && best >= 0) rc = spmm_replan(A, &grid[(size_t)best], transpose, stream);
+    }
+    if (rc == SPMM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_fail(e, "spmm_autotune: sync");
+    cudaFree(X);
+    cudaFree(Y);
+    cudaFree(flush);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc == SPMM_OK) *best_index = best;
+    return rc;
 }

@@ -80,10 +80,10 @@ struct Streamer {
 };
 
 struct Params {
-    int32_t task_nnz = 256;     // nonzeros per short-row task
+    int32_t task_nnz = 512;     // nonzeros per short-row task
     int32_t task_rows = 64;     // rows per short-row task
     int32_t long_row = 512;     // rows longer than this are split
-    int32_t short_max = 31;     // rows with more nonzeros are "long"
+    int32_t short_max = 63;     // rows with more nonzeros are "long"
     int32_t x_evict_last = 1;   // L2 policy of the X gathers (1 = evict-last)
     int64_t slot_bytes = 256ll << 20;   // streaming staging slot (column indices)
     int32_t fail_block = 0;

@@ -83,6 +83,10 @@ _lib.spmm_nmf.argtypes = [_P, _i32, _i32, _P, _P, ctypes.c_int, ctypes.c_double,
 _lib.spmm_nmf.restype = ctypes.c_int
 _lib.spmm_eigs.argtypes = [_P, _i32, _i32, _i32, _i32, ctypes.c_double, ctypes.c_int, _P, _P, _P, _P, _P, _P]
 _lib.spmm_eigs.restype = ctypes.c_int
+_lib.spmm_replan.argtypes = [_P, ctypes.POINTER(spmm_opts), _i32, _P]
+_lib.spmm_replan.restype = ctypes.c_int
+_lib.spmm_autotune.argtypes = [_P, _i32, ctypes.c_int, _i32, _P, _i32, _i32, ctypes.POINTER(_i32), _P, _P]
+_lib.spmm_autotune.restype = ctypes.c_int
 _lib.spmm_last_error.argtypes = []
 _lib.spmm_last_error.restype = ctypes.c_char_p
 
@@ -244,6 +248,31 @@ def spmm_eigs(h, nev, V0, block=16, max_basis=64, max_restarts=100, tol=1e-6, xt
                           _ptr(V0), _P(ev.ctypes.data), _ptr(evecs), _P(rs.ctypes.data), ctypes.byref(nr),
                           _stream_handle(stream)))
     return ev, rs, nr.value
+
+
+def spmm_replan(h, opts: spmm_opts | None = None, transpose=0, stream=None):
+    _check(_lib.spmm_replan(h, ctypes.byref(opts) if opts is not None else None, int(transpose),
+                            _stream_handle(stream)))
+
+
+BUILTIN_GRID = [dict(task_nnz=tn, short_max=sm, long_row=512, x_l2_policy=pol)
+                for tn in (128, 256, 512) for sm in (7, 15, 31, 63) for pol in (1, 2) if sm < tn]
+
+
+def spmm_autotune(h, k, xtype=SPMM_F32, transpose=0, candidates=None, reps=3, stream=None):
+    """Returns (best index, times_ms, candidate list as dicts); the handle is
+    left on the best plan."""
+    if candidates is None:
+        cands, arr, n = BUILTIN_GRID, None, len(BUILTIN_GRID)
+    else:
+        cands = list(candidates)
+        n = len(cands)
+        arr = (spmm_opts * n)(*[spmm_opts(**c) for c in cands])
+    times = np.zeros(n, dtype=np.float64)
+    best = _i32(-1)
+    _check(_lib.spmm_autotune(h, int(k), int(xtype), int(transpose), arr, n if arr is not None else 0, int(reps),
+                              ctypes.byref(best), _P(times.ctypes.data), _stream_handle(stream)))
+    return best.value, times, cands
 
 
 def spmm_get_info(h) -> dict:

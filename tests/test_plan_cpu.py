@@ -77,7 +77,7 @@ def test_plan_classes(sp):
     their own, hub rows are split into segments of at most task_nnz."""
     deg = np.array([0, 1, 2, 40, 0, 3, 600, 5, 1500], dtype=np.int64)
     rp = np.concatenate([[0], np.cumsum(deg)])
-    tasks, n_split, n_seg = sp.spmm_plan_tasks(rp)
+    tasks, n_split, n_seg = sp.spmm_plan_tasks(rp, sp.spmm_opts(task_nnz=256, short_max=31, long_row=512))
     kinds = [(int(t[0]), int(t[1])) for t in tasks[:-1]]
     assert kinds[0] == (0, 3)                        # rows 0-2 packed
     assert kinds[1] == (3, 0)                        # degree 40 > 31: long

@@ -72,6 +72,11 @@ typedef enum {
  *   debug_fail_block streaming mode, for tests: 1 + the block before
  *              which the streamer reports an injected copy failure and
  *              drains (0 = never)
+ *   compensated  1 = long rows and hub-row segments are summed with
+ *              Neumaier's compensated float32 summation (each product's
+ *              rounding error recovered with an FMA) and split rows'
+ *              segment partials are combined the same way; 0 = plain
+ *              float32 sums (default)
  */
 typedef struct {
     int32_t task_nnz;
@@ -81,7 +86,7 @@ typedef struct {
     int32_t x_l2_policy;
     int32_t stream_slot_kib;
     int32_t debug_fail_block;
-    int32_t reserved;
+    int32_t compensated;
 } spmm_opts;
 
 /* Plan statistics reported by spmm_get_info. */
@@ -134,6 +139,42 @@ typedef struct {
 int spmm_create_csr(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, int64_t nnz,
                     const int64_t* row_ptr, const int32_t* col_idx, const void* values,
                     spmm_dtype vtype, uint32_t flags, const spmm_opts* opts, void* stream);
+
+/*
+ * spmm_create_tiles -- build a handle from the paper's tiled storage
+ * (Section 3.2, SCSR + COO): the matrix is cut into tile x tile blocks
+ * (tile <= 32768, so row and column numbers fit 15 bits).  In one tile's
+ * data, every non-empty row with two or more entries is a header word
+ * (0x8000 | row within the tile) followed by its column words (top bit clear,
+ * column within the tile); then come the single-entry rows as (row, column)
+ * word pairs (the coordinate section, which needs no end-of-row test).  The
+ * storage of a tile with nnr non-empty rows and nnz entries of c value bytes
+ * is 2*nnr + (2 + c)*nnz bytes.  Values follow the storage order.
+ *   tile_row, tile_col  position of the tile in tile units
+ *   n_scsr_words        16-bit words of the header/column section
+ *   n_coo               single-entry rows stored as pairs after it
+ *   data                n_scsr_words + 2*n_coo words (host)
+ *   values              values in storage order (host), or NULL in every tile
+ * The tiles are decoded on the host into CSR (a row's entries in tile order,
+ * then storage order; repeated entries are kept and add up) and passed to
+ * spmm_create_csr with the same vtype, flags, opts and stream.
+ * Errors: SPMM_ERR_ARG (tile > 32768, NULL), SPMM_ERR_FORMAT (a column word
+ * before any header, a header without columns, a top bit set in a coordinate
+ * word, a row or column outside the tile or the matrix, values in some tiles
+ * only), and those of spmm_create_csr.
+ */
+typedef struct {
+    int64_t tile_row;
+    int64_t tile_col;
+    int64_t n_scsr_words;
+    int64_t n_coo;
+    const uint16_t* data;
+    const void* values;
+} spmm_tile_desc;
+
+int spmm_create_tiles(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, int32_t tile, int64_t n_tiles,
+                      const spmm_tile_desc* tiles, spmm_dtype vtype, uint32_t flags, const spmm_opts* opts,
+                      void* stream);
 
 /*
  * spmm_create_batched -- one handle for a batch of independent graphs, stored

@@ -46,6 +46,7 @@ static void free_dev(DevCSR& d) {
     cudaFree(d.tasks);
     cudaFree(d.splits);
     cudaFree(d.partials);
+    cudaFree(d.partials_comp);
     d = DevCSR{};
 }
 
@@ -91,6 +92,13 @@ static int build_orientation(DevCSR& d, int64_t n_rows, int64_t n_cols, const in
         size_t pb = (size_t)d.n_slots * kSlotStride * sizeof(float);
         if ((e = cudaMalloc((void**)&d.partials, pb)) != cudaSuccess) { d.partials = nullptr; return cuda_fail(e, "partials"); }
         *bytes += (int64_t)pb;
+        if (p.compensated) {
+            if ((e = cudaMalloc((void**)&d.partials_comp, pb)) != cudaSuccess) {
+                d.partials_comp = nullptr;
+                return cuda_fail(e, "partials");
+            }
+            *bytes += (int64_t)pb;
+        }
     }
     // the plan vectors die with this frame: finish the copies first
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "create sync");
@@ -110,6 +118,7 @@ static Params resolve_params(const spmm_opts* opts) {
         if (opts->x_l2_policy == 2) prm.x_evict_last = 1;
         if (opts->stream_slot_kib > 0) prm.slot_bytes = (int64_t)opts->stream_slot_kib << 10;
         if (opts->debug_fail_block > 0) prm.fail_block = opts->debug_fail_block;
+        prm.compensated = opts->compensated ? 1 : 0;
     }
     prm.task_nnz = std::min(std::max(prm.task_nnz, 32), kMaxTaskNnz);
     prm.task_rows = std::min(std::max(prm.task_rows, 1), kMaxTaskRows);
@@ -284,6 +293,12 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
     return SPMM_OK;
 }
 
+int create_from_host_csr(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t* row_ptr,
+                         const int32_t* col_idx, const void* values, spmm_dtype vtype, uint32_t flags,
+                         const spmm_opts* opts, cudaStream_t s, const char* who) {
+    return create_impl(out, n_rows, n_cols, nnz, row_ptr, col_idx, values, vtype, flags, opts, s, who);
+}
+
 }  // namespace spmm
 
 extern "C" int spmm_create_csr(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, int64_t nnz,
@@ -441,9 +456,11 @@ int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int3
     a.status = A->status;
     a.wait_ns = kWaitNs;
     a.x_evict_last = A->params.x_evict_last;
+    a.compensated = d.partials_comp != nullptr || (A->params.compensated && d.n_slots == 0);
+    a.partials_comp = d.partials_comp;
     cudaError_t e = launch_rows(a, xtype, vmode, vec, ch, s);
     if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: task kernel");
-    e = launch_combine(d.splits, d.n_splits, d.partials, Y, ldy, k, s);
+    e = launch_combine(d.splits, d.n_splits, d.partials, Y, ldy, k, s, d.partials_comp);
     if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: combine kernel");
     return SPMM_OK;
 }
@@ -557,23 +574,27 @@ static int replan_orientation(DevCSR& d, const Params& p, cudaStream_t s, int64_
     if (e != cudaSuccess) return cuda_fail(e, "replan: row pointers");
     HostPlan plan = build_plan(rp.data(), d.n_rows, p);
     int4 *tasks = nullptr, *splits = nullptr;
-    float* partials = nullptr;
+    float *partials = nullptr, *pcomp = nullptr;
     int64_t added = 0;
+    const size_t pb = (size_t)plan.n_slots * kSlotStride * sizeof(float);
     if ((e = upload(&tasks, plan.tasks.data(), plan.tasks.size(), 0, s, &added)) != cudaSuccess ||
         (e = upload(&splits, plan.splits.data(), plan.splits.size(), 0, s, &added)) != cudaSuccess ||
-        (plan.n_slots > 0 &&
-         (e = cudaMalloc((void**)&partials, (size_t)plan.n_slots * kSlotStride * sizeof(float))) != cudaSuccess)) {
+        (plan.n_slots > 0 && (e = cudaMalloc((void**)&partials, pb)) != cudaSuccess) ||
+        (plan.n_slots > 0 && p.compensated && (e = cudaMalloc((void**)&pcomp, pb)) != cudaSuccess)) {
         cudaFree(tasks);
         cudaFree(splits);
+        cudaFree(partials);
         return cuda_fail(e, "replan: upload");
     }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "replan: sync");
     *bytes -= (int64_t)((d.n_tasks + 1) * sizeof(int4) + d.n_splits * sizeof(int4) +
-                        d.n_slots * kSlotStride * sizeof(float));
-    *bytes += added + (int64_t)(plan.n_slots * kSlotStride * sizeof(float));
+                        d.n_slots * kSlotStride * sizeof(float) * (d.partials_comp ? 2 : 1));
+    *bytes += added + (int64_t)(pb * (pcomp ? 2 : 1));
     cudaFree(d.tasks);
     cudaFree(d.splits);
     cudaFree(d.partials);
+    cudaFree(d.partials_comp);
+    d.partials_comp = pcomp;
     d.tasks = tasks;
     d.n_tasks = (int64_t)plan.tasks.size() - 1;
     d.splits = splits;
@@ -602,8 +623,9 @@ extern "C" int spmm_replan(spmm_mat_t A, const spmm_opts* opts, int32_t transpos
     const Params p = resolve_params(opts);
     const int rc = replan_orientation(transpose ? A->tr : A->fwd, p, (cudaStream_t)stream, &A->device_bytes);
     if (rc == SPMM_OK) {
-        // the L2 policy is a launch parameter shared by both orientations
+        // the L2 policy and compensation are launch parameters shared by both orientations
         A->params.x_evict_last = p.x_evict_last;
+        A->params.compensated = p.compensated;
         if (!transpose) A->params = p;
     }
     return rc;

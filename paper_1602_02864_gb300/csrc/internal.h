@@ -52,6 +52,7 @@ struct DevCSR {
     int64_t n_splits = 0;
     int64_t n_segments = 0;
     float* partials = nullptr;      // scratch: n_slots x kSlotStride floats
+    float* partials_comp = nullptr; // compensation terms of the partials (compensated plans only)
     int64_t n_slots = 0;
 };
 
@@ -87,6 +88,7 @@ struct Params {
     int32_t x_evict_last = 1;   // L2 policy of the X gathers (1 = evict-last)
     int64_t slot_bytes = 256ll << 20;   // streaming staging slot (column indices)
     int32_t fail_block = 0;
+    int32_t compensated = 0;            // compensated sums for long rows and hub segments
 };
 
 }  // namespace spmm
@@ -149,6 +151,8 @@ struct FwdArgs {
     int32_t* status;      // set to 1 if a staging wait times out
     uint64_t wait_ns;     // bound of every staging wait
     int32_t x_evict_last; // gather X with the L2 evict-last policy
+    int32_t compensated;  // long rows / hub segments: compensated summation
+    float* partials_comp; // compensation term of each segment partial (compensated only)
 };
 
 // rows_*.cu: launch the task kernel for one X dtype.  vmode: 0 pattern,
@@ -159,7 +163,7 @@ cudaError_t launch_rows_f16(const FwdArgs& a, int vmode, int vec, int ch, cudaSt
 
 // combine.cu: Y[row] = sum of the split row's partials in segment order.
 cudaError_t launch_combine(const int4* splits, int64_t n_splits, const float* partials, float* Y,
-                           int64_t ldy, int32_t k, cudaStream_t s);
+                           int64_t ldy, int32_t k, cudaStream_t s, const float* partials_comp = nullptr);
 
 // status.cu: a kernel whose staging wait can never complete, to exercise
 // the bounded-wait error path.

@@ -280,7 +280,7 @@ __device__ __forceinline__ void issue_task(const FwdArgs& a, const int4 d0, cons
 #define SPMM_MIN_BLOCKS 4         // resident blocks per SM the register budget targets
 #endif
 
-template <typename XT, int VMODE, int VEC, int CH>
+template <typename XT, int VMODE, int VEC, int CH, bool COMP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOCKS) rows_kernel(FwdArgs a) {
     using Lay = Layout<VMODE>;
     // nonzeros in flight per lane group
@@ -429,6 +429,79 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
                     for (int c = 0; c < CH; ++c)
                         if (act[c]) store_y<VEC>(dst + (li + c * LANES) * VEC, acc[c]);
                 }
+            } else if (COMP) {
+                // one long row or hub segment, compensated: Neumaier summation of
+                // the products, whose own rounding error fmaf recovers exactly
+                float acc[CH][VEC], cmp[CH][VEC];
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[c][v] = 0.f, cmp[c][v] = 0.f;
+                for (int i = g; i < n; i += G * U) {
+                    XVec<XT, VEC> xv[U][CH];
+                    float av[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int idx = i + u * G;
+                        if (idx < n) {
+                            const int64_t cidx = st.col[idx];
+                            av[u] = staged_val<VMODE>(st.val, idx);
+#pragma unroll
+                            for (int c = 0; c < CH; ++c)
+                                if (act[c]) xv[u][c].load(xb + cidx * a.ldx + c * LANES * VEC, xpol);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (i + u * G < n) {
+#pragma unroll
+                            for (int c = 0; c < CH; ++c)
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) {
+                                    const float x = xv[u][c].get(v);
+                                    const float p = av[u] * x;
+                                    const float pe = fmaf(av[u], x, -p);       // exact product error
+                                    const float t = acc[c][v] + p;
+                                    const float e = (fabsf(acc[c][v]) >= fabsf(p)) ? (acc[c][v] - t) + p
+                                                                                   : (p - t) + acc[c][v];
+                                    cmp[c][v] += e + pe;
+                                    acc[c][v] = t;
+                                }
+                        }
+                }
+                for (int off = LANES; off < 32; off <<= 1)
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            const float s2 = __shfl_xor_sync(0xffffffffu, acc[c][v], off);
+                            const float c2 = __shfl_xor_sync(0xffffffffu, cmp[c][v], off);
+                            const float t = acc[c][v] + s2;
+                            const float e = (fabsf(acc[c][v]) >= fabsf(s2)) ? (acc[c][v] - t) + s2
+                                                                            : (s2 - t) + acc[c][v];
+                            cmp[c][v] += c2 + e;
+                            acc[c][v] = t;
+                        }
+                if (g == 0) {
+                    if (d0.y == 0) {                   // whole row: one rounding of sum + compensation
+#pragma unroll
+                        for (int c = 0; c < CH; ++c)
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) acc[c][v] += cmp[c][v];
+                        float* dst = a.Y + (int64_t)d0.x * a.ldy;
+#pragma unroll
+                        for (int c = 0; c < CH; ++c)
+                            if (act[c]) store_y<VEC>(dst + (li + c * LANES) * VEC, acc[c]);
+                    } else {                           // segment: keep the pair for the combine pass
+                        const int64_t slot = (int64_t)(-d0.y - 1) * kSlotStride;
+#pragma unroll
+                        for (int c = 0; c < CH; ++c)
+                            if (act[c]) {
+                                store_y<VEC>(a.partials + slot + (li + c * LANES) * VEC, acc[c]);
+                                store_y<VEC>(a.partials_comp + slot + (li + c * LANES) * VEC, cmp[c]);
+                            }
+                    }
+                }
             } else {
                 // one long row or one hub segment: nonzeros g, g+G, ... per group
                 float acc[CH][VEC];
@@ -481,7 +554,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
     }
 }
 
-template <typename XT, int VMODE, int VEC, int CH>
+template <typename XT, int VMODE, int VEC, int CH, bool COMP>
 cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     using Lay = Layout<VMODE>;
     static int blocks_per_sm = 0;   // per instantiation, computed once
@@ -489,14 +562,14 @@ cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     if (blocks_per_sm == 0) {
         cudaError_t e;
         if (Lay::kBlock > 48 * 1024) {
-            e = cudaFuncSetAttribute(rows_kernel<XT, VMODE, VEC, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(rows_kernel<XT, VMODE, VEC, CH, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      Lay::kBlock);
             if (e != cudaSuccess) return e;
         }
         int dev = 0, nb = 0, sms = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rows_kernel<XT, VMODE, VEC, CH>,
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rows_kernel<XT, VMODE, VEC, CH, COMP>,
                                                                kWarpsPerBlock * 32, Lay::kBlock)) != cudaSuccess)
             return e;
         num_sms = sms;
@@ -505,15 +578,16 @@ cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     const int64_t want = (a.n_tasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const int64_t cap = (int64_t)blocks_per_sm * num_sms;
     const dim3 grid((unsigned)(want < cap ? want : cap));
-    rows_kernel<XT, VMODE, VEC, CH><<<grid, kWarpsPerBlock * 32, Lay::kBlock, s>>>(a);
+    rows_kernel<XT, VMODE, VEC, CH, COMP><<<grid, kWarpsPerBlock * 32, Lay::kBlock, s>>>(a);
     return cudaGetLastError();
 }
 
 template <typename XT>
 cudaError_t launch_rows_t(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
     if (a.n_tasks <= 0) return cudaSuccess;
-#define SPMM_LAUNCH(VM, V, C) \
-    if (vmode == VM && vec == V && ch == C) return launch_one<XT, VM, V, C>(a, s);
+#define SPMM_LAUNCH(VM, V, C)                                                   \
+    if (vmode == VM && vec == V && ch == C)                                     \
+        return a.compensated ? launch_one<XT, VM, V, C, true>(a, s) : launch_one<XT, VM, V, C, false>(a, s);
     if constexpr (sizeof(XT) == 4) {
         SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1) SPMM_LAUNCH(0, 1, 2)
         SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1) SPMM_LAUNCH(1, 1, 2)

@@ -161,6 +161,8 @@ extern "C" int spmm_apply_csr_static(int64_t n_rows, int64_t n_cols, int64_t nnz
     a.status = status;
     a.wait_ns = 2000000000ull;
     a.x_evict_last = 1;
+    a.compensated = 0;
+    a.partials_comp = nullptr;
     if (xtype == SPMM_F32) e = launch_rows_f32(a, vmode, vec, ch, s);
     else if (xtype == SPMM_BF16) e = launch_rows_bf16(a, vmode, vec, ch, s);
     else e = launch_rows_f16(a, vmode, vec, ch, s);

@@ -122,6 +122,12 @@ int stream_setup(spmm_mat* A, const int64_t* row_ptr, const int32_t* col_idx, co
         if ((e = cudaMalloc((void**)&d.partials, (size_t)d.n_slots * kSlotStride * sizeof(float))) != cudaSuccess)
             return cuda_fail(e, "streaming: partials");
         *bytes += (int64_t)d.n_slots * kSlotStride * sizeof(float);
+        if (A->params.compensated) {
+            if ((e = cudaMalloc((void**)&d.partials_comp, (size_t)d.n_slots * kSlotStride * sizeof(float))) !=
+                cudaSuccess)
+                return cuda_fail(e, "streaming: partials");
+            *bytes += (int64_t)d.n_slots * kSlotStride * sizeof(float);
+        }
     }
     S.bytes_per_apply = nnz * 4 + (int64_t)(values ? nnz * vsize : 0) + (n + 1) * 8;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "streaming: set-up");
@@ -146,6 +152,8 @@ int stream_apply(const spmm_mat* A, const void* X, int64_t ldx, int32_t k, int32
     a.status = A->status;
     a.wait_ns = kWaitNs;
     a.x_evict_last = A->params.x_evict_last;
+    a.compensated = d.partials_comp != nullptr || (A->params.compensated && d.n_slots == 0);
+    a.partials_comp = d.partials_comp;
     int rc = SPMM_OK;
     cudaError_t e = cudaSuccess;
     for (size_t bi = 0; bi < S.blocks.size(); ++bi) {
@@ -178,7 +186,8 @@ int stream_apply(const spmm_mat* A, const void* X, int64_t ldx, int32_t k, int32
         if ((e = launch_rows(a, xtype, vmode, vec, ch, s)) != cudaSuccess) break;
         if ((e = cudaEventRecord(S.freed[slot], s)) != cudaSuccess) break;
     }
-    if (rc == SPMM_OK && e == cudaSuccess) e = launch_combine(d.splits, d.n_splits, d.partials, Y, ldy, k, s);
+    if (rc == SPMM_OK && e == cudaSuccess)
+        e = launch_combine(d.splits, d.n_splits, d.partials, Y, ldy, k, s, d.partials_comp);
     if (rc != SPMM_OK || e != cudaSuccess) {
         // drain what was enqueued before reporting, so the slots are idle again
         cudaStreamSynchronize(S.copy);

@@ -37,7 +37,12 @@ class SpmmError(RuntimeError):
 class spmm_opts(ctypes.Structure):
     _fields_ = [("task_nnz", ctypes.c_int32), ("task_rows", ctypes.c_int32), ("long_row", ctypes.c_int32),
                 ("short_max", ctypes.c_int32), ("x_l2_policy", ctypes.c_int32), ("stream_slot_kib", ctypes.c_int32),
-                ("debug_fail_block", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("debug_fail_block", ctypes.c_int32), ("compensated", ctypes.c_int32)]
+
+
+class spmm_tile_desc(ctypes.Structure):
+    _fields_ = [("tile_row", ctypes.c_int64), ("tile_col", ctypes.c_int64), ("n_scsr_words", ctypes.c_int64),
+                ("n_coo", ctypes.c_int64), ("data", ctypes.c_void_p), ("values", ctypes.c_void_p)]
 
 
 class spmm_info(ctypes.Structure):
@@ -87,6 +92,9 @@ _lib.spmm_replan.argtypes = [_P, ctypes.POINTER(spmm_opts), _i32, _P]
 _lib.spmm_replan.restype = ctypes.c_int
 _lib.spmm_autotune.argtypes = [_P, _i32, ctypes.c_int, _i32, _P, _i32, _i32, ctypes.POINTER(_i32), _P, _P]
 _lib.spmm_autotune.restype = ctypes.c_int
+_lib.spmm_create_tiles.argtypes = [ctypes.POINTER(_P), _i64, _i64, _i32, _i64, ctypes.POINTER(spmm_tile_desc),
+                                   ctypes.c_int, _u32, ctypes.POINTER(spmm_opts), _P]
+_lib.spmm_create_tiles.restype = ctypes.c_int
 _lib.spmm_last_error.argtypes = []
 _lib.spmm_last_error.restype = ctypes.c_char_p
 
@@ -275,6 +283,22 @@ def spmm_autotune(h, k, xtype=SPMM_F32, transpose=0, candidates=None, reps=3, st
     return best.value, times, cands
 
 
+def spmm_create_tiles(n_rows, n_cols, tile, tiles, flags=0, opts: spmm_opts | None = None, stream=None) -> _P:
+    """tiles: list of (tile_row, tile_col, scsr_words uint16, coo_pairs uint16 [n,2], values float32 or None)."""
+    keep = []
+    arr = (spmm_tile_desc * max(len(tiles), 1))()
+    for i, (tr, tc, scsr, coo, vals) in enumerate(tiles):
+        data = np.ascontiguousarray(np.concatenate([np.asarray(scsr, np.uint16), np.asarray(coo, np.uint16).ravel()]))
+        v = None if vals is None else np.ascontiguousarray(vals, dtype=np.float32)
+        keep += [data, v]
+        arr[i] = spmm_tile_desc(tr, tc, len(scsr), len(coo), data.ctypes.data, None if v is None else v.ctypes.data)
+    h = _P(0)
+    _check(_lib.spmm_create_tiles(ctypes.byref(h), int(n_rows), int(n_cols), int(tile), len(tiles), arr, SPMM_F32,
+                                  int(flags), ctypes.byref(opts) if opts is not None else None,
+                                  _stream_handle(stream)))
+    return h
+
+
 def spmm_get_info(h) -> dict:
     info = spmm_info()
     _check(_lib.spmm_get_info(h, ctypes.byref(info)))
@@ -299,6 +323,15 @@ class SparseMatrix:
                               None if values is None else np.ascontiguousarray(values))
             row_ptr, col_idx, values = self._borrowed
         self.handle = spmm_create_csr(n_rows, n_cols, row_ptr, col_idx, values, flags, opts, stream)
+
+    @classmethod
+    def from_tiles(cls, n_rows, n_cols, tile, tiles, transpose=False, opts: spmm_opts | None = None, stream=None):
+        """Handle from SCSR + COO tiles (see spmm_create_tiles)."""
+        self = cls.__new__(cls)
+        self.n_rows, self.n_cols = int(n_rows), int(n_cols)
+        self.handle = spmm_create_tiles(n_rows, n_cols, tile, tiles, SPMM_WANT_TRANSPOSE if transpose else 0, opts,
+                                        stream)
+        return self
 
     @classmethod
     def batched(cls, graphs, transpose=False, weighted=True, opts: spmm_opts | None = None, stream=None):

@@ -64,6 +64,13 @@ def metric_name(args):
     return f"SpMM nonzeros/s (R-MAT scale {args.scale}, k sweep {args.ks}{pr}, FP32 X)"
 
 
+# DRAM bytes of one PageRank iteration (product on A^T + combine + update +
+# reduce) measured with ncu on the default workload (R-MAT scale 24, edge
+# factor 16); see profiles/pagerank_iteration_rmat24.md.  Only reported for
+# that workload.
+PAGERANK_ITER_TRAFFIC = {(24, 16): 1.8803e9}
+
+
 def pagerank_iter_bytes(nnz, n):
     """Algorithmic bytes of one PageRank iteration: the A^T product at k = 1
     (column indices, row pointers, z in, y out) plus the update (y, x read and
@@ -519,6 +526,7 @@ def main():
                     "nnz_per_s": nnz / (it_ms / 1e3), "alg_GBps": B / (it_ms / 1e3) / 1e9,
                     "roofline_frac": B / (it_ms / 1e3) / 1e9 / peak_gbs, "sum_x": float(xh.sum()),
                     "min_x": float(xh.min()), "residual_first_last": [float(pr_res[0][0]), float(pr_res[0][-1])]}
+        pagerank["traffic"] = PAGERANK_ITER_TRAFFIC.get((args.scale, args.edge_factor))
         if ms > statistics.mean(per_k[kdom]):
             dom = pagerank
             dom_name = ("PageRank iteration: rows_kernel on A^T (k=1, f32) + update + reduce; "
@@ -627,7 +635,7 @@ def main():
             "bf16": bf16,
             "parity_max_err_over_absprod": parity,
             "roofline": {"bound": "hbm", "achieved": dom["alg_GBps"], "peak": peak_gbs, "unit": "GB/s",
-                         "frac": dom["roofline_frac"], "traffic": None, "kernel": dom_name,
+                         "frac": dom["roofline_frac"], "traffic": dom.get("traffic"), "kernel": dom_name,
                          "peak_kind": peak_kind},
             "pagerank": pagerank,
             "e2e": e2e,

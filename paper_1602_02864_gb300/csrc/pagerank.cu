@@ -7,9 +7,9 @@
 // with the transposed matrix: y = A^T z with z[v] = x[v] / L(v).
 //
 // One iteration = the task kernel on A^T (k = 1, float32) + one fused
-// elementwise kernel (new ranks, the next z, FP64 per-block partial sums of the
-// L1 change and of the dangling mass) + a one-block kernel adding the partials
-// in a fixed order.  All iterations are captured into one CUDA graph and
+// elementwise kernel (new ranks, the next z = x' * (1/L), FP64 per-block
+// partial sums of the L1 change and of the dangling mass) + a one-block kernel
+// adding the partials in a fixed order.  All iterations are captured into one CUDA graph and
 // launched once.  Ranks are float32; every reduction is FP64 and run-to-run
 // deterministic.
 #include <vector>
@@ -34,26 +34,38 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return s;
 }
 
-// outdeg[v] = L(v) as float (0 for dangling vertices); x = x0 or 1/N.
-__global__ void pr_init_kernel(const int64_t* __restrict__ row_ptr, int64_t n, float* __restrict__ outdeg,
+// inv[v] = 1/L(v) as float (0 marks a dangling vertex, L = 0); x = x0 or 1/N.
+__global__ void pr_init_kernel(const int64_t* __restrict__ row_ptr, int64_t n, float* __restrict__ inv,
                                float* __restrict__ x, const float* __restrict__ x0) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        outdeg[i] = (float)(row_ptr[i + 1] - row_ptr[i]);
+        const int64_t L = row_ptr[i + 1] - row_ptr[i];
+        inv[i] = L > 0 ? 1.0f / (float)L : 0.f;
         x[i] = x0 ? x0[i] : (float)(1.0 / (double)n);
     }
 }
 
+// One rank update of element i (float32): x' = base + d*y; returns |x' - x|,
+// writes z' = x' / L and adds x' to dang for a dangling vertex.
+__device__ __forceinline__ float pr_elem(float y, float& x, float inv, float base, float d, float& z, float& dang) {
+    const float xn = fmaf(d, y, base);
+    const float r = fabsf(xn - x);
+    x = xn;
+    z = xn * inv;
+    if (inv == 0.f) dang += xn;
+    return r;
+}
+
 // z = x / L (0 where L = 0); per-block partial of the dangling mass.
-__global__ void pr_scale_kernel(const float* __restrict__ x, const float* __restrict__ outdeg, int64_t n,
+__global__ void pr_scale_kernel(const float* __restrict__ x, const float* __restrict__ inv, int64_t n,
                                 float* __restrict__ z, double* __restrict__ part_dang) {
     __shared__ double sh[32];
     double dang = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float L = outdeg[i], xi = x[i];
-        if (L > 0.f) z[i] = xi / L;
-        else { z[i] = 0.f; dang += (double)xi; }
+        const float xi = x[i], iv = inv[i];
+        z[i] = xi * iv;
+        if (iv == 0.f) dang += (double)xi;
     }
     const double s = block_sum(dang, sh);
     if (threadIdx.x == 0) part_dang[blockIdx.x] = s;
@@ -61,20 +73,44 @@ __global__ void pr_scale_kernel(const float* __restrict__ x, const float* __rest
 
 // x' = (1-d)/N + d*D/N + d*y, with D the dangling mass of x (scal[0]);
 // partials of sum |x' - x| and of the dangling mass of x'; z' = x' / L.
-__global__ void pr_update_kernel(const float* __restrict__ y, float* __restrict__ x, const float* __restrict__ outdeg,
+// Float4 accesses; the per-element arithmetic is float32 and every group of
+// four is added to FP64 per-thread sums, then to FP64 block partials.
+__global__ void pr_update_kernel(const float* __restrict__ y, float* __restrict__ x, const float* __restrict__ inv,
                                  int64_t n, double d, const double* __restrict__ scal, float* __restrict__ z,
                                  double* __restrict__ part_res, double* __restrict__ part_dang) {
     __shared__ double sh[32];
-    const double base = (1.0 - d) / (double)n + d * scal[0] / (double)n;
+    const float base = (float)((1.0 - d) / (double)n + d * scal[0] / (double)n);
+    const float df = (float)d;
     double res = 0.0, dang = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float xn = (float)(base + d * (double)y[i]);
-        res += fabs((double)xn - (double)x[i]);
-        x[i] = xn;
-        const float L = outdeg[i];
-        if (L > 0.f) z[i] = xn / L;
-        else { z[i] = 0.f; dang += (double)xn; }
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vec = ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)z) | ((uintptr_t)inv)) & 15) == 0;
+    int64_t done = 0;
+    if (vec) {
+        const int64_t n4 = n >> 2;
+        for (int64_t i = tid; i < n4; i += stride) {
+            const float4 y4 = reinterpret_cast<const float4*>(y)[i];
+            float4 x4 = reinterpret_cast<const float4*>(x)[i];
+            const float4 v4 = reinterpret_cast<const float4*>(inv)[i];
+            float4 z4;
+            float dg = 0.f, r = 0.f;
+            r += pr_elem(y4.x, x4.x, v4.x, base, df, z4.x, dg);
+            r += pr_elem(y4.y, x4.y, v4.y, base, df, z4.y, dg);
+            r += pr_elem(y4.z, x4.z, v4.z, base, df, z4.z, dg);
+            r += pr_elem(y4.w, x4.w, v4.w, base, df, z4.w, dg);
+            reinterpret_cast<float4*>(x)[i] = x4;
+            reinterpret_cast<float4*>(z)[i] = z4;
+            res += (double)r;
+            dang += (double)dg;
+        }
+        done = n4 << 2;
+    }
+    for (int64_t i = done + tid; i < n; i += stride) {   // tail (or unaligned buffers)
+        float xi = x[i], zi, dg = 0.f;
+        res += (double)pr_elem(y[i], xi, inv[i], base, df, zi, dg);
+        x[i] = xi;
+        z[i] = zi;
+        dang += (double)dg;
     }
     const double s1 = block_sum(res, sh);
     const double s2 = block_sum(dang, sh);
@@ -129,8 +165,8 @@ extern "C" int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float*
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "spmm_pagerank: device query");
     const int nblk = sms * 8;
-    // workspace: outdeg, z, y (float n each), partials (2 x nblk), scalar, residuals
-    float *outdeg = nullptr, *z = nullptr, *y = nullptr;
+    // workspace: 1/out-degree, z, y (float n each), partials (2 x nblk), scalar, residuals
+    float *inv_deg = nullptr, *z = nullptr, *y = nullptr;
     double *part = nullptr, *scal = nullptr, *dres = nullptr;
     cudaStream_t s = nullptr;
     cudaGraph_t graph = nullptr;
@@ -139,7 +175,7 @@ extern "C" int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float*
     auto fail = [&](cudaError_t err, const char* what) { rc = cuda_fail(err, what); };
     do {
         if ((e = cudaStreamSynchronize(user)) != cudaSuccess) { fail(e, "spmm_pagerank: stream"); break; }
-        if ((e = cudaMalloc((void**)&outdeg, n * sizeof(float))) != cudaSuccess ||
+        if ((e = cudaMalloc((void**)&inv_deg, n * sizeof(float))) != cudaSuccess ||
             (e = cudaMalloc((void**)&z, n * sizeof(float))) != cudaSuccess ||
             (e = cudaMalloc((void**)&y, n * sizeof(float))) != cudaSuccess ||
             (e = cudaMalloc((void**)&part, 2 * (size_t)nblk * sizeof(double))) != cudaSuccess ||
@@ -153,8 +189,8 @@ extern "C" int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float*
             break;
         }
         // set-up outside the graph
-        pr_init_kernel<<<nblk, kPrThreads, 0, s>>>(A->fwd.row_ptr, n, outdeg, x, x0);
-        pr_scale_kernel<<<nblk, kPrThreads, 0, s>>>(x, outdeg, n, z, part);
+        pr_init_kernel<<<nblk, kPrThreads, 0, s>>>(A->fwd.row_ptr, n, inv_deg, x, x0);
+        pr_scale_kernel<<<nblk, kPrThreads, 0, s>>>(x, inv_deg, n, z, part);
         pr_reduce_kernel<<<1, kPrThreads, 0, s>>>(part, nullptr, nblk, scal, nullptr);
         if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "spmm_pagerank: init"); break; }
         // warm the task kernel's launch configuration outside the capture
@@ -168,7 +204,7 @@ extern "C" int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float*
             for (int32_t t = 0; t < iters && rc == SPMM_OK; ++t) {
                 rc = apply_dev(A, 1, z, 1, 1, SPMM_F32, y, 1, s);
                 if (rc != SPMM_OK) break;
-                pr_update_kernel<<<nblk, kPrThreads, 0, s>>>(y, x, outdeg, n, damping, scal, z, part + nblk, part);
+                pr_update_kernel<<<nblk, kPrThreads, 0, s>>>(y, x, inv_deg, n, damping, scal, z, part + nblk, part);
                 pr_reduce_kernel<<<1, kPrThreads, 0, s>>>(part, part + nblk, nblk, scal, dres + t);
             }
             cudaError_t ec = cudaStreamEndCapture(s, &graph);
@@ -198,7 +234,7 @@ extern "C" int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float*
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (s) cudaStreamDestroy(s);
-    cudaFree(outdeg);
+    cudaFree(inv_deg);
     cudaFree(z);
     cudaFree(y);
     cudaFree(part);

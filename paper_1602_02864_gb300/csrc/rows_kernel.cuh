@@ -388,7 +388,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
                 for (int j = lane; j < nr; j += 32) {
                     const int s = (int)(st.rp[j] - e0), e = (int)(st.rp[j + 1] - e0);
                     float acc = 0.f;
-                    for (int i = s; i < e; ++i) acc += __int_as_float(prod[i]);
+                    for (int i = s; i < e; i += 4) {          // four loads in flight, added in order
+                        const float p0 = __int_as_float(prod[i]);
+                        const float p1 = i + 1 < e ? __int_as_float(prod[i + 1]) : 0.f;
+                        const float p2 = i + 2 < e ? __int_as_float(prod[i + 2]) : 0.f;
+                        const float p3 = i + 3 < e ? __int_as_float(prod[i + 3]) : 0.f;
+                        acc += p0;
+                        if (i + 1 < e) acc += p1;
+                        if (i + 2 < e) acc += p2;
+                        if (i + 3 < e) acc += p3;
+                    }
                     __stcs(a.Y + (int64_t)(d0.x + j) * a.ldy, acc);
                 }
                 fence_proxy_async();   // the products were written where the next copy lands

@@ -51,9 +51,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ceiling", action="store_true", help="skip the gather-ceiling probes")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--pagerank-iters", type=int, default=30)
-    ap.add_argument("--workload", default="ksweep", choices=["ksweep", "streaming", "nmf-batched", "eigs"],
+    ap.add_argument("--workload", default="ksweep",
+                    choices=["ksweep", "streaming", "nmf-batched", "eigs", "gather-ceiling"],
                     help="ksweep: the headline SpMM sweep + PageRank; the others measure the streaming mode, "
                          "the batched launch with NMF and the eigensolver")
     return ap.parse_args()
@@ -207,6 +209,15 @@ def reference_arm(args, rank, world):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def profiler_range(on: bool):
+    """cudaProfilerStart/Stop around the timed steps (no-ops without a profiler)."""
+    import torch
+    try:
+        (torch.cuda.profiler.start if on else torch.cuda.profiler.stop)()
+    except Exception:
+        pass
 
 
 def aggregate(units_per_rank, t_local, world):
@@ -414,6 +425,20 @@ def workload_eigs(args):
                      "symrmat-lcc-eigs-top8-block16", "bf16", {"results": out})
 
 
+def workload_gather_ceiling(args):
+    """Random-row gather ceilings: row sizes 4..256 B from tables inside L2
+    (64 MB) and in DRAM (8 GB)."""
+    from paper_1602_02864_gb300 import spmm
+    out = {}
+    for rb in (4, 8, 16, 32, 64, 128, 256):
+        for tb, name in (((64 << 20), "l2_64MB"), ((8 << 30), "dram_8GB")):
+            r, b = spmm.spmm_probe_gather(tb, rb)
+            out[f"{rb}B_{name}"] = {"rows_per_s": r, "GBps": b / 1e9}
+    best = max(v["rows_per_s"] for v in out.values())
+    return base_line(args, "random row-gather ceiling (rows/s)", best, "rows/s", 0.0, "gather-ceiling", "f32",
+                     {"probes": out})
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -424,7 +449,8 @@ def main():
     if args.workload != "ksweep":
         import torch
         torch.cuda.set_device(local)
-        fn = {"streaming": workload_streaming, "nmf-batched": workload_nmf_batched, "eigs": workload_eigs}
+        fn = {"streaming": workload_streaming, "nmf-batched": workload_nmf_batched, "eigs": workload_eigs,
+              "gather-ceiling": workload_gather_ceiling}
         print(json.dumps(fn[args.workload](args)), flush=True)
         return
 
@@ -501,6 +527,8 @@ def main():
     peak_gbs, peak_kind = load_peaks()
     with ClockSampler(local) as clk:
         barrier()
+        # a profiler started with --profile-from-start off records only these steps
+        profiler_range(True)
         for _ in range(args.steps):
             flush.zero_()
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -514,6 +542,7 @@ def main():
                 pr_ms.append(ev[-1][0].elapsed_time(ev[-1][1]))
                 ms.append(pr_ms[-1])
             step_ms.append(sum(ms))
+        profiler_range(False)
         barrier()
     value, t_total = aggregate(nnz * (len(ks) + args.pagerank_iters) * args.steps, sum(step_ms) / 1e3, world)
 
@@ -542,6 +571,24 @@ def main():
             dom = pagerank
             dom_name = ("PageRank iteration: rows_kernel on A^T (k=1, f32) + update + reduce; "
                         f"{args.pagerank_iters} per CUDA-graph launch, timed per call")
+
+    # ---- measured gather ceilings for each k (the dominant cost: one X row
+    # per nonzero): uniformly random rows from a table of X's size, and this
+    # matrix's own column stream replayed with nothing else of the SpMM
+    ceilings = {}
+    for k in ([] if args.no_ceiling else ks):
+        rb = 4
+        while rb < 4 * k:
+            rb *= 2
+        uni, _ = spmm.spmm_probe_gather(N * k * 4, rb)
+        own, _ = spmm.spmm_probe_gather_cols(h.handle, 0, 4 * k)
+        ceilings[str(k)] = {"table_MB": round(N * k * 4 / 1e6, 1), "uniform_rows_per_s": uni,
+                            "matrix_stream_rows_per_s": own,
+                            "frac_of_matrix_stream": breakdown[str(k)]["nnz_per_s"] / own}
+    pr_ceiling = None
+    if args.pagerank_iters and not args.no_ceiling:
+        own, _ = spmm.spmm_probe_gather_cols(h.handle, 1, 4)
+        pr_ceiling = {"matrix_stream_rows_per_s": own, "frac_of_matrix_stream": pagerank["nnz_per_s"] / own}
 
     # ---- BF16 X: speedup over FP32 and error on sampled rows vs the oracle
     import oracle
@@ -667,6 +714,11 @@ def main():
                          "frac": dom["roofline_frac"], "traffic": dom.get("traffic"), "kernel": dom_name,
                          "peak_kind": peak_kind},
             "pagerank": pagerank,
+            "gather_ceiling": {"per_k": ceilings, "pagerank": pr_ceiling,
+                               "note": "rows/s of gathers alone: uniform = random rows of an X-sized table "
+                                       "(spmm_probe_gather); matrix_stream = one row per stored entry of this "
+                                       "matrix in storage order (spmm_probe_gather_cols); frac = the SpMM's "
+                                       "nnz/s over that"},
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),

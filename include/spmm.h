@@ -394,6 +394,51 @@ int spmm_replan(spmm_mat_t A, const spmm_opts* opts, int32_t transpose, void* st
 int spmm_autotune(spmm_mat_t A, int32_t k, spmm_dtype xtype, int32_t transpose, const spmm_opts* candidates,
                   int32_t n_candidates, int32_t reps, int32_t* best_index, double* times_ms, void* stream);
 
+/*
+ * spmm_probe_gather -- diagnostic: the measured rate of uniformly random row
+ * gathers on this GPU, the practical ceiling of the SpMM's dominant cost
+ * (one X row per nonzero).  Gathers rows of row_bytes (a power of two,
+ * 4..256) at random row indices from a zero-filled table of table_bytes
+ * (4 KiB .. 64 GiB; below the L2 size the rows come from L2, above it from
+ * DRAM), eight loads in flight per lane, about 4 GB gathered.
+ *   rows_per_s, bytes_per_s   host out
+ * Synchronises `stream`; allocates its table.  Not a paper operation.
+ */
+int spmm_probe_gather(int64_t table_bytes, int32_t row_bytes, double* rows_per_s, double* bytes_per_s,
+                      void* stream);
+
+/*
+ * spmm_probe_gather_cols -- diagnostic: the gather ceiling of one matrix.
+ * Replays the handle's own column-index stream (forward, or the transpose if
+ * `transpose` != 0) in storage order, gathering for every stored entry one
+ * row of row_bytes (a multiple of 4, 4..256; 4*k for an FP32 X of k columns)
+ * from a zero table of n_cols rows, and nothing else of the SpMM.  Five runs
+ * back to back (the table stays warm, as X does across iterations).
+ *   rows_per_s   host out: stored entries per second
+ *   bytes_per_s  host out: (row_bytes + 4) per entry per second
+ * Synchronises `stream`; allocates its table.  SPMM_ERR_UNSUPPORTED for a
+ * streaming handle.  Not a paper operation.
+ */
+int spmm_probe_gather_cols(spmm_mat_t A, int32_t transpose, int32_t row_bytes, double* rows_per_s,
+                           double* bytes_per_s, void* stream);
+
+/*
+ * spmm_svds -- the nsv largest singular values of A (any shape) and their
+ * right singular vectors, by the spmm_eigs method applied to A^T A without
+ * forming it: each block product is A V (X in FP32 or BF16) followed by
+ * A^T (A V) (the intermediate kept in FP32).  The paper computes singular
+ * values of the directed Page graph with its eigensolver (Section 5.5.2).
+ *   A           handle created with SPMM_WANT_TRANSPOSE
+ *   V0          device double[n_cols * block] start block
+ *   svals       host double[nsv], descending (square roots of the Ritz values)
+ *   right_vecs  device double[n_cols * nsv] or NULL
+ *   resid       host double[nsv] or NULL: ||A^T A v - s^2 v||_2
+ *   other arguments and errors as spmm_eigs (max_basis <= min(64, n_cols))
+ */
+int spmm_svds(spmm_mat_t A, int32_t nsv, int32_t block, int32_t max_basis, int32_t max_restarts, double tol,
+              spmm_dtype xtype, const double* V0, double* svals, double* right_vecs, double* resid,
+              int32_t* restarts_out, void* stream);
+
 /* spmm_get_info -- plan statistics of a handle (host call, no GPU work). */
 int spmm_get_info(spmm_mat_t A, spmm_info* info);
 

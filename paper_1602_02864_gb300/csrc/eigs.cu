@@ -205,6 +205,8 @@ struct Eig {
     int64_t n;
     int m, b;
     int xtype;
+    int op = 0;              // 0: S V;  1: A^T (A V)
+    float* T1 = nullptr;     // A V (op 1), n_rows x b
     cudaStream_t s;
     double *V = nullptr, *AV = nullptr, *W = nullptr, *W2 = nullptr, *part = nullptr, *small = nullptr;
     double *U = nullptr, *AU = nullptr, *theta = nullptr;
@@ -233,7 +235,13 @@ struct Eig {
     // Y = S * block (block: n x b FP64 with leading dimension ld) into out (ld m)
     int apply_block(const double* blk, int64_t ld, double* out, int64_t ldo) {
         f64_to_x_kernel<<<grid, kEigThreads, 0, s>>>(blk, ld, b, n, Xs, xtype == SPMM_BF16);
-        const int rc = apply_dev(A, 0, Xs, b, b, xtype, Yf, b, s);
+        int rc;
+        if (op == 0) {
+            rc = apply_dev(A, 0, Xs, b, b, xtype, Yf, b, s);
+        } else {   // A^T (A V): the intermediate stays float32
+            rc = apply_dev(A, 0, Xs, b, b, xtype, T1, b, s);
+            if (rc == SPMM_OK) rc = apply_dev(A, 1, T1, b, b, SPMM_F32, Yf, b, s);
+        }
         if (rc != SPMM_OK) return rc;
         f32_to_f64_kernel<<<grid, kEigThreads, 0, s>>>(Yf, b, n, out, ldo);
         return SPMM_OK;
@@ -262,12 +270,13 @@ struct Eig {
 
 using namespace spmm;
 
-extern "C" int spmm_eigs(spmm_mat_t S, int32_t nev, int32_t block, int32_t max_basis, int32_t max_restarts,
-                         double tol, spmm_dtype xtype, const double* V0, double* evals, double* evecs,
-                         double* resid, int32_t* restarts_out, void* stream) {
+static int eigs_impl(spmm_mat_t S, int op, int32_t nev, int32_t block, int32_t max_basis, int32_t max_restarts,
+                     double tol, spmm_dtype xtype, const double* V0, double* evals, double* evecs, double* resid,
+                     int32_t* restarts_out, void* stream) {
     if (!S || !V0 || !evals) { set_error("spmm_eigs: NULL argument"); return SPMM_ERR_ARG; }
-    const int64_t n = S->fwd.n_rows;
-    if (S->fwd.n_cols != n || n < 1) { set_error("spmm_eigs: the matrix must be square"); return SPMM_ERR_ARG; }
+    const int64_t n = op ? S->fwd.n_cols : S->fwd.n_rows;
+    if (op == 0 && (S->fwd.n_cols != n || n < 1)) { set_error("spmm_eigs: the matrix must be square"); return SPMM_ERR_ARG; }
+    if (op == 1 && !S->has_tr) { set_error("spmm_svds: needs SPMM_WANT_TRANSPOSE at create"); return SPMM_ERR_ARG; }
     if (block < 1 || block > 32 || nev < 1 || nev > block + 32 || max_basis > kEigMaxBasis ||
         max_basis < nev + 2 * block || max_basis > n || max_restarts < 0 || !(tol > 0.0)) {
         set_error("spmm_eigs: need 1 <= block <= 32, nev + 2*block <= max_basis <= min(64, n), max_restarts >= 0, "
@@ -288,6 +297,7 @@ extern "C" int spmm_eigs(spmm_mat_t S, int32_t nev, int32_t block, int32_t max_b
     E.m = max_basis;
     E.b = block;
     E.xtype = xtype;
+    E.op = op;
     E.grid = std::max(1, sms * 8);
     E.chunk = std::max<int64_t>(1024, (n + 1023) / 1024);
     E.nchunks = (int)((n + E.chunk - 1) / E.chunk);
@@ -308,7 +318,9 @@ extern "C" int spmm_eigs(spmm_mat_t S, int32_t nev, int32_t block, int32_t max_b
             (e = cudaMalloc((void**)&E.small, (size_t)m * m * sizeof(double))) != cudaSuccess ||
             (e = cudaMalloc((void**)&E.theta, (size_t)m * sizeof(double))) != cudaSuccess ||
             (e = cudaMalloc((void**)&E.Yf, (size_t)n * b * sizeof(float))) != cudaSuccess ||
-            (e = cudaMalloc(&E.Xs, (size_t)n * b * sizeof(float))) != cudaSuccess) {
+            (e = cudaMalloc(&E.Xs, (size_t)n * b * sizeof(float))) != cudaSuccess ||
+            (op && (e = cudaMalloc((void**)&E.T1, (size_t)std::max<int64_t>(S->fwd.n_rows, 1) * b * sizeof(float))) !=
+                       cudaSuccess)) {
             fail(e, "spmm_eigs: workspace");
             break;
         }
@@ -400,6 +412,23 @@ extern "C" int spmm_eigs(spmm_mat_t S, int32_t nev, int32_t block, int32_t max_b
         cudaStreamDestroy(E.s);
     }
     cudaFree(E.V); cudaFree(E.AV); cudaFree(E.U); cudaFree(E.AU); cudaFree(E.W); cudaFree(E.W2);
-    cudaFree(E.part); cudaFree(E.small); cudaFree(E.theta); cudaFree(E.Yf); cudaFree(E.Xs);
+    cudaFree(E.part); cudaFree(E.small); cudaFree(E.theta); cudaFree(E.Yf); cudaFree(E.Xs); cudaFree(E.T1);
+    return rc;
+}
+
+extern "C" int spmm_eigs(spmm_mat_t S, int32_t nev, int32_t block, int32_t max_basis, int32_t max_restarts,
+                         double tol, spmm_dtype xtype, const double* V0, double* evals, double* evecs,
+                         double* resid, int32_t* restarts_out, void* stream) {
+    return eigs_impl(S, 0, nev, block, max_basis, max_restarts, tol, xtype, V0, evals, evecs, resid, restarts_out,
+                     stream);
+}
+
+extern "C" int spmm_svds(spmm_mat_t A, int32_t nsv, int32_t block, int32_t max_basis, int32_t max_restarts,
+                         double tol, spmm_dtype xtype, const double* V0, double* svals, double* right_vecs,
+                         double* resid, int32_t* restarts_out, void* stream) {
+    const int rc = eigs_impl(A, 1, nsv, block, max_basis, max_restarts, tol, xtype, V0, svals, right_vecs, resid,
+                             restarts_out, stream);
+    if (rc == SPMM_OK)
+        for (int i = 0; i < nsv; ++i) svals[i] = std::sqrt(std::max(0.0, svals[i]));
     return rc;
 }

@@ -160,6 +160,10 @@ struct FwdArgs {
 cudaError_t launch_rows_f32(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
 cudaError_t launch_rows_bf16(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
 cudaError_t launch_rows_f16(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
+// one lane per X row (ch == 1, lanes_log2 == 0); called by the three above
+cudaError_t launch_rows_f32_one(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
+cudaError_t launch_rows_bf16_one(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
+cudaError_t launch_rows_f16_one(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
 
 // combine.cu: Y[row] = sum of the split row's partials in segment order.
 cudaError_t launch_combine(const int4* splits, int64_t n_splits, const float* partials, float* Y,

@@ -5,7 +5,8 @@
 namespace spmm {
 
 cudaError_t launch_rows_bf16(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
-    return launch_rows_t<__nv_bfloat16>(a, vmode, vec, ch, s);
+    if (ch == 1 && a.lanes_log2 == 0) return launch_rows_bf16_one(a, vmode, vec, ch, s);
+    return launch_rows_t<__nv_bfloat16, false>(a, vmode, vec, ch, s);
 }
 
 }  // namespace spmm

@@ -5,7 +5,8 @@
 namespace spmm {
 
 cudaError_t launch_rows_f32(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
-    return launch_rows_t<float>(a, vmode, vec, ch, s);
+    if (ch == 1 && a.lanes_log2 == 0) return launch_rows_f32_one(a, vmode, vec, ch, s);
+    return launch_rows_t<float, false>(a, vmode, vec, ch, s);
 }
 
 }  // namespace spmm

@@ -276,17 +276,35 @@ __device__ __forceinline__ void issue_task(const FwdArgs& a, const int4 d0, cons
 #ifndef SPMM_UNROLL_BYTES
 #define SPMM_UNROLL_BYTES 64      // X bytes in flight per lane
 #endif
+#ifndef SPMM_K1_FLAT
+#define SPMM_K1_FLAT 1            // k = 1 short-row runs: flat gather through shared memory
+#endif
+#ifndef SPMM_MERGE
+#define SPMM_MERGE 1              // one lane per X row: merge-based short-row runs
+#endif
 #ifndef SPMM_MIN_BLOCKS
 #define SPMM_MIN_BLOCKS 4         // resident blocks per SM the register budget targets
 #endif
 
-template <typename XT, int VMODE, int VEC, int CH, bool COMP>
+// ONE: one lane per X row (k == VEC, CH == 1); the lane geometry is then a
+// compile-time constant and short-row runs take the flat (k = 1) or, for X
+// rows of up to 8 bytes, the merge-based path.
+template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOCKS) rows_kernel(FwdArgs a) {
+    static_assert(!ONE || CH == 1, "one lane per row needs CH == 1");
+    constexpr bool kFlat = ONE && VEC == 1 && SPMM_K1_FLAT;
+    // merge-based runs pay off for X rows of up to 8 bytes; for 16-byte rows
+    // (mostly gathered from DRAM) the row-per-lane walk measured faster
+    constexpr bool kMerge = ONE && !kFlat && SPMM_MERGE && VEC * sizeof(XT) <= 8;
     using Lay = Layout<VMODE>;
     // nonzeros in flight per lane group
     constexpr int kBytes = VEC * CH * (int)sizeof(XT);
     constexpr int kU = SPMM_UNROLL_BYTES / kBytes;
     constexpr int U = kU < 2 ? 2 : (kU > 8 ? 8 : kU);
+#ifndef SPMM_MERGE_UNROLL
+#define SPMM_MERGE_UNROLL 2
+#endif
+    constexpr int UM = U < SPMM_MERGE_UNROLL ? U : SPMM_MERGE_UNROLL;   // merge path: nonzeros in flight per lane
     extern __shared__ __align__(128) unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* wb = smem + w * Lay::kWarp;
@@ -303,7 +321,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
     __syncwarp();
 
     // lane geometry
-    const int lg = a.lanes_log2;
+    const int lg = ONE ? 0 : a.lanes_log2;
     const int LANES = 1 << lg, G = 32 >> lg;
     const int g = lane >> lg, li = lane & (LANES - 1);
     bool act[CH];
@@ -357,7 +375,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
             }
             st.rp = reinterpret_cast<const int64_t*>(buf + Lay::kRpOff) + (d0.x & 1);
 
-            if (VEC == 1 && CH == 1 && lg == 0 && d0.y > 0) {
+            if (kFlat && d0.y > 0) {
                 // k = 1, run of short rows: every lane gathers the task's
                 // nonzeros as one flat array (lane, lane+32, ...) and writes each
                 // product over its staged column index; then lane j adds the
@@ -401,7 +419,109 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
                     __stcs(a.Y + (int64_t)(d0.x + j) * a.ldy, acc);
                 }
                 fence_proxy_async();   // the products were written where the next copy lands
-            } else if (d0.y > 0) {
+            } else if (kMerge && d0.y > 0) {
+                // run of short rows, one lane per X row (merge-based): the task's
+                // nonzeros are cut into 32 equal contiguous pieces, lane l taking
+                // piece l, so every lane gathers about n/32 rows of X whatever
+                // the row lengths.  A lane walks its piece in order and stores
+                // the rows that lie wholly inside it.  A row that crosses piece
+                // boundaries leaves a tail partial in each lane it continues out
+                // of and a head partial in the lane where it ends; a segmented
+                // scan (shfl_up) over the lanes' tails, keyed by row,
+                // adds the tails, and the ending lane adds its head last.
+                const int nr = d0.y;
+                for (int j = lane; j < nr; j += 32)       // rows without nonzeros
+                    if (st.rp[j] == st.rp[j + 1]) {
+                        float z[VEC];
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) z[v] = 0.f;
+                        store_y<VEC>(a.Y + (int64_t)(d0.x + j) * a.ldy, z);
+                    }
+                const int per = (n + 31) >> 5;
+                const int cs = min(n, lane * per), ce = min(n, cs + per);
+                float tail[VEC], head[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) tail[v] = 0.f, head[v] = 0.f;
+                int key = -1 - lane;                      // tail row, or a key no other lane has
+                int hrow = -1;                            // head row
+                if (cs < ce) {
+                    // r: the row holding nonzero cs (largest r with rp[r] <= e0 + cs)
+                    int lo = 0, hi = nr - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if ((int)(st.rp[mid] - e0) <= cs) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    int r = lo;
+                    int rs = (int)(st.rp[r] - e0), re = (int)(st.rp[r + 1] - e0);
+                    float acc[VEC];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+                    for (int i = cs; i < ce; i += UM) {
+                        XVec<XT, VEC> xv[UM];
+                        float av[UM];
+#pragma unroll
+                        for (int u = 0; u < UM; ++u)
+                            if (i + u < ce) {
+                                const int64_t cidx = st.col[i + u];
+                                av[u] = staged_val<VMODE>(st.val, i + u);
+                                xv[u].load(xb + cidx * a.ldx, xpol);
+                            }
+#pragma unroll
+                        for (int u = 0; u < UM; ++u)
+                            if (i + u < ce) {
+                                while (i + u >= re) {             // row r ended inside the piece
+                                    if (rs < re) {
+                                        if (rs >= cs) {
+                                            store_y<VEC>(a.Y + (int64_t)(d0.x + r) * a.ldy, acc);
+                                        } else {
+                                            hrow = r;
+#pragma unroll
+                                            for (int v = 0; v < VEC; ++v) head[v] = acc[v];
+                                        }
+                                    }
+#pragma unroll
+                                    for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+                                    ++r;
+                                    rs = re;
+                                    re = (int)(st.rp[r + 1] - e0);
+                                }
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) acc[v] = fmaf(av[u], xv[u].get(v), acc[v]);
+                            }
+                    }
+                    // the row holding nonzero ce - 1
+                    if (re > ce) {
+                        key = r;
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) tail[v] = acc[v];
+                    } else if (rs >= cs) {
+                        store_y<VEC>(a.Y + (int64_t)(d0.x + r) * a.ldy, acc);
+                    } else {
+                        hrow = r;
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) head[v] = acc[v];
+                    }
+                }
+                // segmented inclusive scan of the tails (a row's tails sit in
+                // consecutive lanes, so equal keys bound a segment)
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int kup = __shfl_up_sync(0xffffffffu, key, off);
+                    float up[VEC];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) up[v] = __shfl_up_sync(0xffffffffu, tail[v], off);
+                    if (lane >= off && kup == key)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) tail[v] += up[v];
+                }
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    const float prev = __shfl_up_sync(0xffffffffu, tail[v], 1);
+                    head[v] = prev + head[v];
+                }
+                if (hrow >= 0) store_y<VEC>(a.Y + (int64_t)(d0.x + hrow) * a.ldy, head);
+            } else if (!kFlat && !kMerge && d0.y > 0) {
                 // run of short rows: lane group g owns rows g, g+G, ...
                 const int nr = d0.y;
                 for (int j = g; j < nr; j += G) {
@@ -563,7 +683,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
     }
 }
 
-template <typename XT, int VMODE, int VEC, int CH, bool COMP>
+template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE>
 cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     using Lay = Layout<VMODE>;
     static int blocks_per_sm = 0;   // per instantiation, computed once
@@ -571,14 +691,14 @@ cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     if (blocks_per_sm == 0) {
         cudaError_t e;
         if (Lay::kBlock > 48 * 1024) {
-            e = cudaFuncSetAttribute(rows_kernel<XT, VMODE, VEC, CH, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(rows_kernel<XT, VMODE, VEC, CH, COMP, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      Lay::kBlock);
             if (e != cudaSuccess) return e;
         }
         int dev = 0, nb = 0, sms = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rows_kernel<XT, VMODE, VEC, CH, COMP>,
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rows_kernel<XT, VMODE, VEC, CH, COMP, ONE>,
                                                                kWarpsPerBlock * 32, Lay::kBlock)) != cudaSuccess)
             return e;
         num_sms = sms;
@@ -587,25 +707,38 @@ cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     const int64_t want = (a.n_tasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const int64_t cap = (int64_t)blocks_per_sm * num_sms;
     const dim3 grid((unsigned)(want < cap ? want : cap));
-    rows_kernel<XT, VMODE, VEC, CH, COMP><<<grid, kWarpsPerBlock * 32, Lay::kBlock, s>>>(a);
+    rows_kernel<XT, VMODE, VEC, CH, COMP, ONE><<<grid, kWarpsPerBlock * 32, Lay::kBlock, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename XT>
+template <typename XT, bool ONE>
 cudaError_t launch_rows_t(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
     if (a.n_tasks <= 0) return cudaSuccess;
-#define SPMM_LAUNCH(VM, V, C)                                                   \
-    if (vmode == VM && vec == V && ch == C)                                     \
-        return a.compensated ? launch_one<XT, VM, V, C, true>(a, s) : launch_one<XT, VM, V, C, false>(a, s);
-    if constexpr (sizeof(XT) == 4) {
-        SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1) SPMM_LAUNCH(0, 1, 2)
-        SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1) SPMM_LAUNCH(1, 1, 2)
+#define SPMM_LAUNCH(VM, V, C)                                                            \
+    if (vmode == VM && vec == V && ch == C)                                              \
+        return a.compensated ? launch_one<XT, VM, V, C, true, ONE>(a, s)                 \
+                             : launch_one<XT, VM, V, C, false, ONE>(a, s);
+    if constexpr (ONE) {
+        if constexpr (sizeof(XT) == 4) {
+            SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1)
+            SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1)
+        } else {
+            constexpr int VM3 = std::is_same<XT, __half>::value ? 3 : 2;  // own-type values
+            SPMM_LAUNCH(0, 8, 1) SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1)
+            SPMM_LAUNCH(1, 8, 1) SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1)
+            SPMM_LAUNCH(VM3, 8, 1) SPMM_LAUNCH(VM3, 4, 1) SPMM_LAUNCH(VM3, 2, 1) SPMM_LAUNCH(VM3, 1, 1)
+        }
     } else {
-        constexpr int VM3 = std::is_same<XT, __half>::value ? 3 : 2;  // own-type values
-        SPMM_LAUNCH(0, 8, 1) SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1) SPMM_LAUNCH(0, 1, 2)
-        SPMM_LAUNCH(1, 8, 1) SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1) SPMM_LAUNCH(1, 1, 2)
-        SPMM_LAUNCH(VM3, 8, 1) SPMM_LAUNCH(VM3, 4, 1) SPMM_LAUNCH(VM3, 2, 1) SPMM_LAUNCH(VM3, 1, 1)
-        SPMM_LAUNCH(VM3, 1, 2)
+        if constexpr (sizeof(XT) == 4) {
+            SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1) SPMM_LAUNCH(0, 1, 2)
+            SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1) SPMM_LAUNCH(1, 1, 2)
+        } else {
+            constexpr int VM3 = std::is_same<XT, __half>::value ? 3 : 2;
+            SPMM_LAUNCH(0, 8, 1) SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1) SPMM_LAUNCH(0, 1, 2)
+            SPMM_LAUNCH(1, 8, 1) SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1) SPMM_LAUNCH(1, 1, 2)
+            SPMM_LAUNCH(VM3, 8, 1) SPMM_LAUNCH(VM3, 4, 1) SPMM_LAUNCH(VM3, 2, 1) SPMM_LAUNCH(VM3, 1, 1)
+            SPMM_LAUNCH(VM3, 1, 2)
+        }
     }
 #undef SPMM_LAUNCH
     return cudaErrorInvalidValue;

@@ -95,6 +95,14 @@ _lib.spmm_autotune.restype = ctypes.c_int
 _lib.spmm_create_tiles.argtypes = [ctypes.POINTER(_P), _i64, _i64, _i32, _i64, ctypes.POINTER(spmm_tile_desc),
                                    ctypes.c_int, _u32, ctypes.POINTER(spmm_opts), _P]
 _lib.spmm_create_tiles.restype = ctypes.c_int
+_lib.spmm_probe_gather.argtypes = [_i64, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                   _P]
+_lib.spmm_probe_gather.restype = ctypes.c_int
+_lib.spmm_probe_gather_cols.argtypes = [_P, _i32, _i32, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), _P]
+_lib.spmm_probe_gather_cols.restype = ctypes.c_int
+_lib.spmm_svds.argtypes = [_P, _i32, _i32, _i32, _i32, ctypes.c_double, ctypes.c_int, _P, _P, _P, _P, _P, _P]
+_lib.spmm_svds.restype = ctypes.c_int
 _lib.spmm_last_error.argtypes = []
 _lib.spmm_last_error.restype = ctypes.c_char_p
 
@@ -299,6 +307,35 @@ def spmm_create_tiles(n_rows, n_cols, tile, tiles, flags=0, opts: spmm_opts | No
     return h
 
 
+def spmm_probe_gather(table_bytes, row_bytes, stream=None):
+    """(rows/s, bytes/s) of uniformly random row gathers from a table."""
+    r, b = ctypes.c_double(0), ctypes.c_double(0)
+    _check(_lib.spmm_probe_gather(int(table_bytes), int(row_bytes), ctypes.byref(r), ctypes.byref(b),
+                                  _stream_handle(stream)))
+    return r.value, b.value
+
+
+def spmm_probe_gather_cols(h, transpose, row_bytes, stream=None):
+    """(rows/s, bytes/s) of gathering one table row per stored entry of the
+    handle's column-index stream."""
+    r, b = ctypes.c_double(0), ctypes.c_double(0)
+    _check(_lib.spmm_probe_gather_cols(h, int(bool(transpose)), int(row_bytes), ctypes.byref(r), ctypes.byref(b),
+                                       _stream_handle(stream)))
+    return r.value, b.value
+
+
+def spmm_svds(h, nsv, V0, block=16, max_basis=64, max_restarts=100, tol=1e-6, xtype=SPMM_F32, right_vecs=None,
+              stream=None):
+    """Top-nsv singular values of A (via A^T A): (svals, residuals, restarts)."""
+    sv = np.zeros(nsv, dtype=np.float64)
+    rs = np.zeros(nsv, dtype=np.float64)
+    nr = ctypes.c_int32(0)
+    _check(_lib.spmm_svds(h, int(nsv), int(block), int(max_basis), int(max_restarts), float(tol), int(xtype),
+                          _ptr(V0), _P(sv.ctypes.data), _ptr(right_vecs), _P(rs.ctypes.data), ctypes.byref(nr),
+                          _stream_handle(stream)))
+    return sv, rs, nr.value
+
+
 def spmm_get_info(h) -> dict:
     info = spmm_info()
     _check(_lib.spmm_get_info(h, ctypes.byref(info)))
@@ -341,6 +378,10 @@ class SparseMatrix:
         self.n_cols = int(sum(g.n_cols for g in graphs))
         self.handle = spmm_create_batched(graphs, SPMM_WANT_TRANSPOSE if transpose else 0, opts, stream, weighted)
         return self
+
+    def svds(self, nsv, V0, **kw):
+        """Top-nsv singular values (needs transpose=True): (svals, residuals, restarts)."""
+        return spmm_svds(self.handle, nsv, V0, **kw)
 
     def eigs(self, nev, V0, **kw):
         """Top-nev eigenpairs of a symmetric matrix: (evals, residuals, restarts)."""

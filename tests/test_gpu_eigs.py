@@ -68,3 +68,20 @@ def test_eigs_argument_errors(sp):
     with pytest.raises(sp.SpmmError):                       # basis larger than n
         h.eigs(4, start_block(n, 8), block=8, max_basis=200)
     h.close()
+
+
+def test_svds_matches_dense_svd(sp):
+    """Top singular values of a directed R-MAT graph (via A^T A) against
+    numpy's dense SVD."""
+    import torch
+    A = synth.rmat_csr(11, seed=4, weighted=True)
+    D = graphs.dense_of(A)
+    ref = np.linalg.svd(D, compute_uv=False)[:6]
+    h = sp.SparseMatrix.from_csr(A, transpose=True)
+    V = torch.zeros((A.n_cols, 6), dtype=torch.float64, device="cuda")
+    sv, res, _ = h.svds(6, start_block(A.n_cols, 16), block=16, max_basis=64, max_restarts=300, tol=1e-5,
+                        right_vecs=V)
+    np.testing.assert_allclose(sv, ref, rtol=1e-6)
+    v = V.cpu().numpy()
+    np.testing.assert_allclose(np.linalg.norm(D @ v, axis=0), sv, rtol=1e-5)     # ||A v|| = s
+    h.close()

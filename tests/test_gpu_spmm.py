@@ -121,13 +121,54 @@ def test_plan_shapes_agree(sp, opts):
     h = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, transpose=True, opts=o)
     info = h.info()
     assert info["n_split_rows"] > 0
-    for k in (1, 8, 33):
+    for k in (1, 2, 4, 8, 33):
         X = synth.dense(A.n_cols, k, seed=k, mode="int")
         for tr in (False, True):
             Y = h.apply(to_dev(X), transpose=tr).cpu().numpy().astype(np.float64)
             assert np.array_equal(Y, oracle.spmm(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, X, transpose=tr))
     h.sync_status()
     h.close()
+
+
+@pytest.mark.parametrize("kind", ["uniform", "geometric", "bimodal", "sparse"])
+@pytest.mark.parametrize("task_nnz", [32, 100, 512])
+def test_merge_rows_cross_lane_pieces(sp, kind, task_nnz):
+    """One lane per X row (k = 2 in FP32, k = 2 and 4 in BF16) cuts each
+    short-row run into 32 equal pieces of nonzeros; rows that start before a
+    piece, span several pieces or have no nonzeros must all come out right.
+    Degree mixes: uniform 0..63, geometric, mostly 0..2 with 10% of 30..63,
+    and 0/1."""
+    import torch
+    rng = np.random.default_rng({"uniform": 1, "geometric": 2, "bimodal": 3, "sparse": 4}[kind])
+    n = 3000
+    deg = {"uniform": lambda: rng.integers(0, 64, n),
+           "geometric": lambda: rng.geometric(0.2, n) - 1,
+           "bimodal": lambda: np.where(rng.random(n) < 0.1, rng.integers(30, 64, n), rng.integers(0, 3, n)),
+           "sparse": lambda: rng.integers(0, 2, n)}[kind]()
+    deg = np.minimum(deg, 63)
+    src = np.repeat(np.arange(n), deg)
+    dst = np.concatenate([rng.choice(n, d, replace=False) for d in deg]) if deg.sum() else np.zeros(0, int)
+    A = graphs.csr_from_edges(n, n, src, dst, rng.random(len(src)).astype(np.float32))
+    o = sp.spmm_opts(task_nnz=task_nnz, task_rows=64, long_row=512, short_max=63)
+    hp = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, transpose=True, opts=o)
+    hw = sp.SparseMatrix.from_csr(A, transpose=True, opts=o)
+    for tr in (False, True):
+        X = synth.dense(n, 2, seed=5, mode="int")
+        Y = hp.apply(to_dev(X), transpose=tr).cpu().numpy().astype(np.float64)
+        assert np.array_equal(Y, oracle.spmm(n, n, A.row_ptr, A.col_idx, None, X, transpose=tr))
+        for k in (2, 4):
+            Xb = torch.from_numpy(synth.dense(n, k, seed=6, mode="int")).to(torch.bfloat16).cuda()
+            Yb = hp.apply(Xb, transpose=tr).cpu().numpy().astype(np.float64)
+            ref = oracle.spmm(n, n, A.row_ptr, A.col_idx, None, Xb.float().cpu().numpy(), transpose=tr)
+            assert np.array_equal(Yb, ref)
+        Xf = synth.dense(n, 2, seed=7)
+        Yw = hw.apply(to_dev(Xf), transpose=tr).cpu().numpy()
+        ref = oracle.spmm(n, n, A.row_ptr, A.col_idx, A.values, Xf, transpose=tr)
+        scale = oracle.spmm(n, n, A.row_ptr, A.col_idx, A.values, np.abs(Xf), transpose=tr)
+        assert_close_rel(Yw, ref, scale, 1e-5)
+    hp.sync_status()
+    hp.close()
+    hw.close()
 
 
 def test_edge_cases(sp):

@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--pagerank-iters", type=int, default=30)
     ap.add_argument("--workload", default="ksweep",
-                    choices=["ksweep", "streaming", "nmf-batched", "eigs", "gather-ceiling"],
+                    choices=["ksweep", "streaming", "nmf-batched", "eigs", "gather-ceiling", "vpart"],
                     help="ksweep: the headline SpMM sweep + PageRank; the others measure the streaming mode, "
                          "the batched launch with NMF and the eigensolver")
     return ap.parse_args()
@@ -70,7 +70,7 @@ def metric_name(args):
 # reduce) measured with ncu on the default workload (R-MAT scale 24, edge
 # factor 16); see profiles/pagerank_iteration_rmat24.md.  Only reported for
 # that workload.
-PAGERANK_ITER_TRAFFIC = {(24, 16): 1.8803e9}
+PAGERANK_ITER_TRAFFIC = {(24, 16): 1.8087e9}
 
 
 def pagerank_iter_bytes(nnz, n):
@@ -312,6 +312,81 @@ def workload_streaming(args):
                       "n": N, "nnz": nnz, "setup_s": {"generate": round(t_gen, 1), "create": round(t_create, 1)}})
 
 
+def workload_vpart(args):
+    """Large dense matrices (Section 5.3): X and Y with p = 32 FP32 columns in
+    pinned host memory, multiplied in vertical partitions of c columns
+    (c = 1, 2, 4, 8, 16, 32 kept on the device, one pass over A per group),
+    against the in-memory SpMM with X and Y resident in HBM."""
+    import torch
+    import oracle
+    from paper_1602_02864_gb300 import spmm
+    p = 32
+    t = time.time()
+    A = synth.rmat_csr(args.scale, args.edge_factor << args.scale, seed=0)
+    t_gen = time.time() - t
+    N, nnz = A.n_rows, A.nnz
+    h = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None)
+    Xh = torch.from_numpy(synth.dense(N, p, seed=0)).pin_memory()
+    Yh = torch.empty((N, p), dtype=torch.float32).pin_memory()
+    # in-memory reference: X, Y resident, one k = 32 apply
+    Xd = Xh.cuda()
+    Yd = torch.empty((N, p), device="cuda")
+    for _ in range(args.warmup):
+        h.apply(Xd, Y=Yd)
+    im_ms = event_ms(lambda: h.apply(Xd, Y=Yd), args.steps)
+    rows = np.unique(synth.sample_rows(N, 20_000, seed=7))
+    Xn = Xh.numpy()
+    ref = oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xn, rows, threads=oracle.num_threads())
+    scl = oracle.spmm_rows(A.row_ptr, A.col_idx, None, np.abs(Xn), rows, threads=oracle.num_threads())
+    per_c = {}
+    for c in (1, 2, 4, 8, 16, 32):
+        h.apply_host(Xh, Yh, group_cols=c)
+        ts = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = h.apply_host(Xh, Yh, group_cols=c)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        ms = statistics.median(ts)
+        got = Yh.numpy()[rows].astype(np.float64)
+        err = float((np.abs(got - ref) / np.maximum(scl, 1e-300)).max())
+        link = 2 * N * p * 4
+        per_c[str(c)] = {"groups": g, "ms": round(ms, 3), "nnz_per_s": nnz / (ms / 1e3),
+                         "rel_to_in_memory": im_ms / ms, "link_GBps": link / (ms / 1e3) / 1e9,
+                         "sampled_max_err_over_absprod": err}
+    # Section 3.3's layout: every vertical partition its own contiguous array
+    per_c_parts = {}
+    for c in (1, 2, 4, 8, 16):
+        Xp = [Xh[:, c0:c0 + c].contiguous().pin_memory() for c0 in range(0, p, c)]
+        Yp = [torch.empty((N, c), dtype=torch.float32).pin_memory() for _ in Xp]
+        h.apply_host_parts(Xp, Yp)
+        ts = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.apply_host_parts(Xp, Yp)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        ms = statistics.median(ts)
+        got = torch.cat(Yp, dim=1).numpy()[rows].astype(np.float64)
+        err = float((np.abs(got - ref) / np.maximum(scl, 1e-300)).max())
+        per_c_parts[str(c)] = {"groups": len(Xp), "ms": round(ms, 3), "nnz_per_s": nnz / (ms / 1e3),
+                               "rel_to_in_memory": im_ms / ms, "link_GBps": 2 * N * p * 4 / (ms / 1e3) / 1e9,
+                               "sampled_max_err_over_absprod": err}
+        del Xp, Yp
+    per_c_parts["32"] = per_c["32"]
+    budget = spmm.spmm_vpart_cols(N, N, p, spmm.SPMM_F32, 8 << 30)
+    h.close()
+    best = max(list(per_c.values()) + list(per_c_parts.values()), key=lambda d: d["rel_to_in_memory"])
+    return base_line(args, f"vertically partitioned SpMM, X and Y ({p} FP32 columns) in host memory "
+                           f"(R-MAT scale {args.scale}; nnz/s per call)",
+                     best["nnz_per_s"], "nnz/s", best["ms"], f"rmat{args.scale}-vpart-p{p}", "f32",
+                     {"in_memory_ms": round(im_ms, 3), "per_columns_in_memory": per_c,
+                      "per_columns_in_memory_contiguous_parts": per_c_parts,
+                      "cols_for_8GiB_budget": budget, "n": N, "nnz": nnz,
+                      "timing": "wall clock per call (host buffers; the call returns with Y complete)",
+                      "setup_s": {"generate": round(t_gen, 1)}})
+
+
 def workload_nmf_batched(args):
     """256 Chung-Lu graphs in one block-diagonal handle: batched SpMM vs one
     launch per graph, then NMF (k = 8, 16, 32; 50 steps; FP32 and BF16)."""
@@ -450,7 +525,7 @@ def main():
         import torch
         torch.cuda.set_device(local)
         fn = {"streaming": workload_streaming, "nmf-batched": workload_nmf_batched, "eigs": workload_eigs,
-              "gather-ceiling": workload_gather_ceiling}
+              "gather-ceiling": workload_gather_ceiling, "vpart": workload_vpart}
         print(json.dumps(fn[args.workload](args)), flush=True)
         return
 

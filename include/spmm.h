@@ -224,6 +224,68 @@ int spmm_apply(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype x
 int spmm_sync_status(spmm_mat_t A, void* stream);
 
 /*
+ * spmm_vpart_cols -- host-only: the width of the vertical partitions
+ * (column groups) that spmm_apply_host uses for a dense matrix of p columns
+ * under a device-memory budget.  Section 3.3 splits dense matrices that do
+ * not fit in memory into vertical partitions; Section 3.6 gives the rule:
+ * spend the memory on as many input columns as fit, since each partition
+ * costs one more pass over the sparse matrix.  Each column of a group costs
+ * 2 * (n_in * sizeof(X element) + n_out * 4) bytes (X and Y double-buffered).
+ *   n_in, n_out   rows of X and of Y
+ *   p             columns of X and Y (>= 1)
+ *   xtype         F32, BF16 or F16 (X element size)
+ *   budget_bytes  device bytes available for the group buffers
+ *   cols          out: min(p, 64, columns that fit)
+ * Errors: SPMM_ERR_ARG; SPMM_ERR_OOM if not even one column fits.
+ */
+int spmm_vpart_cols(int64_t n_in, int64_t n_out, int32_t p, spmm_dtype xtype, int64_t budget_bytes,
+                    int32_t* cols);
+
+/*
+ * spmm_apply_host -- Y = A X (or A^T X) with X and Y in HOST memory, in
+ * vertical partitions (Section 3.3; the paper's external medium is SSD, here
+ * it is host memory).  The p columns are processed in groups of g columns,
+ * one pass over A per group: a 2-D copy of the group's columns to the device,
+ * the SpMM, a 2-D copy of the group's result back into Y's columns.  Copy-in,
+ * multiply and copy-out run on three streams with two device buffers for X
+ * and for Y, so consecutive groups overlap.
+ *   A            handle (resident or streaming)
+ *   X            host, row-major, n_in x p with leading dimension ldx >= p
+ *                elements, element type xtype (F32, BF16 or F16); pinned
+ *                memory (cudaHostAlloc / cudaHostRegister) gives full link
+ *                speed, pageable memory works at a lower rate
+ *   Y            host, float32 row-major n_out x p, leading dimension ldy >= p
+ *   transpose    nonzero: Y = A^T X (needs SPMM_WANT_TRANSPOSE)
+ *   group_cols   g in 1..64, or 0 to pick it with spmm_vpart_cols
+ *   budget_bytes device-memory budget for the group buffers when group_cols
+ *                is 0; 0 = 80% of the currently free device memory
+ *   groups_out   out (may be NULL): number of groups = passes over A
+ *   stream       the multiply runs on it, after the work already queued there
+ * The device buffers, two copy streams and their events are kept by the
+ * handle for later calls (freed by spmm_destroy); calls on one handle must not
+ * overlap.  Returns when Y is complete on the host.  The result equals
+ * spmm_apply on the same columns.
+ * Errors: SPMM_ERR_ARG, SPMM_ERR_UNSUPPORTED (value/X type mix),
+ * SPMM_ERR_OOM (the budget holds no column), SPMM_ERR_CUDA.
+ */
+int spmm_apply_host(spmm_mat_t A, const void* X, int64_t ldx, int32_t p, spmm_dtype xtype, float* Y, int64_t ldy,
+                    int32_t transpose, int32_t group_cols, int64_t budget_bytes, int32_t* groups_out,
+                    void* stream);
+
+/*
+ * spmm_apply_host_parts -- as spmm_apply_host for a dense matrix stored as
+ * vertical partitions, each in row-major order (Section 3.3's layout): part i
+ * holds part_cols[i] columns (1..64) as one contiguous host array, so each
+ * group moves with plain contiguous copies instead of strided ones.
+ *   X_parts[i]   host, n_in x part_cols[i] elements of xtype, row-major, no padding
+ *   Y_parts[i]   host, float32 n_out x part_cols[i], row-major, no padding
+ *   n_parts      >= 1; one pass over A per part, in order
+ * Other arguments, buffers, ordering and errors as spmm_apply_host.
+ */
+int spmm_apply_host_parts(spmm_mat_t A, const void* const* X_parts, float* const* Y_parts, const int32_t* part_cols,
+                          int32_t n_parts, spmm_dtype xtype, int32_t transpose, void* stream);
+
+/*
  * spmm_debug_wait_timeout -- diagnostic: run a one-warp kernel whose staging
  * wait can never complete (it announces a transfer it never issues), with a
  * bound of wait_ns nanoseconds, and report SPMM_ERR_TIMEOUT when the bound

@@ -512,6 +512,7 @@ extern "C" int spmm_destroy(spmm_mat_t A) {
     if (!A) return SPMM_OK;
     cudaError_t e = cudaDeviceSynchronize();
     if (A->streaming) stream_release(A);
+    hostio_release(A);
     free_dev(A->fwd);
     free_dev(A->tr);
     cudaFree(A->status);

@@ -93,6 +93,17 @@ struct Params {
 
 }  // namespace spmm
 
+namespace spmm {
+// device buffers, streams and events of spmm_apply_host (created on first use)
+struct HostIO {
+    void* x[2] = {nullptr, nullptr};
+    float* y[2] = {nullptr, nullptr};
+    size_t x_bytes = 0, y_bytes = 0;     // size of each buffer
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev[8] = {};
+};
+}  // namespace spmm
+
 struct spmm_mat {
     spmm::DevCSR fwd;
     spmm::DevCSR tr;
@@ -107,12 +118,16 @@ struct spmm_mat {
     std::vector<double> a2;     // ||A_g||_F^2 per graph
     bool streaming = false;
     spmm::Streamer st;
+    spmm::HostIO hio;
 };
 
 namespace spmm {
 
 // plan.cpp
 HostPlan build_plan(const int64_t* row_ptr, int64_t n_rows, const Params& p);
+
+// vpart.cu
+void hostio_release(spmm_mat* A);
 
 // abi.cu
 void set_error(const std::string& msg);

@@ -103,6 +103,12 @@ _lib.spmm_probe_gather_cols.argtypes = [_P, _i32, _i32, ctypes.POINTER(ctypes.c_
 _lib.spmm_probe_gather_cols.restype = ctypes.c_int
 _lib.spmm_svds.argtypes = [_P, _i32, _i32, _i32, _i32, ctypes.c_double, ctypes.c_int, _P, _P, _P, _P, _P, _P]
 _lib.spmm_svds.restype = ctypes.c_int
+_lib.spmm_vpart_cols.argtypes = [_i64, _i64, _i32, ctypes.c_int, _i64, _P]
+_lib.spmm_vpart_cols.restype = ctypes.c_int
+_lib.spmm_apply_host.argtypes = [_P, _P, _i64, _i32, ctypes.c_int, _P, _i64, _i32, _i32, _i64, _P, _P]
+_lib.spmm_apply_host.restype = ctypes.c_int
+_lib.spmm_apply_host_parts.argtypes = [_P, _P, _P, _P, _i32, ctypes.c_int, _i32, _P]
+_lib.spmm_apply_host_parts.restype = ctypes.c_int
 _lib.spmm_last_error.argtypes = []
 _lib.spmm_last_error.restype = ctypes.c_char_p
 
@@ -307,6 +313,65 @@ def spmm_create_tiles(n_rows, n_cols, tile, tiles, flags=0, opts: spmm_opts | No
     return h
 
 
+def spmm_vpart_cols(n_in, n_out, p, xtype, budget_bytes) -> int:
+    """Column-group width for vertical partitions under a device budget (host only)."""
+    c = ctypes.c_int32(0)
+    _check(_lib.spmm_vpart_cols(int(n_in), int(n_out), int(p), int(xtype), int(budget_bytes), ctypes.byref(c)))
+    return c.value
+
+
+def spmm_apply_host(h, X, Y, transpose=False, group_cols=0, budget_bytes=0, stream=None) -> int:
+    """Y = A X (or A^T X) for host numpy (or pinned CPU torch) matrices, in
+    vertical partitions; returns the number of column groups."""
+    xt, ldx, p, xp = _host_matrix(X)
+    yt, ldy, py, yp = _host_matrix(Y)
+    if yt != SPMM_F32 or py != p:
+        raise ValueError("Y must be float32 with the same number of columns as X")
+    g = ctypes.c_int32(0)
+    _check(_lib.spmm_apply_host(h, xp, ldx, p, xt, yp, ldy, int(bool(transpose)), int(group_cols),
+                                int(budget_bytes), ctypes.byref(g), _stream_handle(stream)))
+    return g.value
+
+
+def spmm_apply_host_parts(h, X_parts, Y_parts, transpose=False, stream=None):
+    """Y = A X for a dense matrix stored as contiguous row-major vertical
+    partitions (lists of host matrices, part i of X and Y with equal columns)."""
+    if len(X_parts) != len(Y_parts) or not X_parts:
+        raise ValueError("need as many Y parts as X parts (at least one)")
+    xs, ys, cols, xtype = [], [], [], None
+    for Xp, Yp in zip(X_parts, Y_parts):
+        xt, ldx, w, xp = _host_matrix(Xp)
+        yt, ldy, wy, yp = _host_matrix(Yp)
+        if ldx != w or ldy != wy or yt != SPMM_F32 or wy != w or (xtype is not None and xt != xtype):
+            raise ValueError("parts must be contiguous, Y float32, same columns, one X dtype")
+        xtype = xt
+        xs.append(xp.value)
+        ys.append(yp.value)
+        cols.append(w)
+    n = len(cols)
+    xa, ya, ca = (ctypes.c_void_p * n)(*xs), (ctypes.c_void_p * n)(*ys), (ctypes.c_int32 * n)(*cols)
+    _check(_lib.spmm_apply_host_parts(h, xa, ya, ca, n, xtype, int(bool(transpose)), _stream_handle(stream)))
+
+
+def _host_matrix(M):
+    """(dtype code, leading dimension, columns, pointer) of a row-major host
+    matrix: a 2-D numpy array or CPU torch tensor with unit column stride."""
+    if isinstance(M, np.ndarray):
+        if M.ndim != 2 or M.strides[1] != M.itemsize or M.strides[0] % M.itemsize:
+            raise ValueError("host matrix must be 2-D with unit column stride")
+        code = {np.dtype(np.float32): SPMM_F32, np.dtype(np.float16): SPMM_F16}.get(M.dtype)
+        if code is None:
+            raise ValueError(f"unsupported host dtype {M.dtype}")
+        return code, M.strides[0] // M.itemsize, M.shape[1], _P(M.ctypes.data)
+    import torch
+    if M.device.type != "cpu" or M.dim() != 2 or M.stride(1) != 1:
+        raise ValueError("host tensor must be a 2-D CPU tensor with unit column stride")
+    code = {torch.float32: SPMM_F32, torch.bfloat16: SPMM_BF16, torch.float16: SPMM_F16}.get(M.dtype)
+    if code is None:
+        raise ValueError(f"unsupported host dtype {M.dtype}")
+    return code, M.stride(0), M.shape[1], _P(M.data_ptr())
+
+
 def spmm_probe_gather(table_bytes, row_bytes, stream=None):
     """(rows/s, bytes/s) of uniformly random row gathers from a table."""
     r, b = ctypes.c_double(0), ctypes.c_double(0)
@@ -378,6 +443,14 @@ class SparseMatrix:
         self.n_cols = int(sum(g.n_cols for g in graphs))
         self.handle = spmm_create_batched(graphs, SPMM_WANT_TRANSPOSE if transpose else 0, opts, stream, weighted)
         return self
+
+    def apply_host(self, X, Y, transpose=False, group_cols=0, budget_bytes=0, stream=None) -> int:
+        """Y = A X with host X, Y (vertical partitions); returns the group count."""
+        return spmm_apply_host(self.handle, X, Y, transpose, group_cols, budget_bytes, stream)
+
+    def apply_host_parts(self, X_parts, Y_parts, transpose=False, stream=None) -> None:
+        """Y = A X for contiguous row-major vertical partitions (host)."""
+        spmm_apply_host_parts(self.handle, X_parts, Y_parts, transpose, stream)
 
     def svds(self, nsv, V0, **kw):
         """Top-nsv singular values (needs transpose=True): (svals, residuals, restarts)."""

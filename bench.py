@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ceiling", action="store_true", help="skip the gather-ceiling probes")
+    ap.add_argument("--reorder", action="store_true",
+                    help="create the handle with SPMM_REORDER (columns relabelled by degree)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--pagerank-iters", type=int, default=30)
     ap.add_argument("--workload", default="ksweep",
@@ -547,7 +549,8 @@ def main():
     A, t_gen = make_graph(args)
     N, nnz = A.n_rows, A.nnz
     t0 = time.time()
-    h = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, transpose=args.pagerank_iters > 0)
+    h = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, transpose=args.pagerank_iters > 0,
+                          reorder=args.reorder)
     torch.cuda.synchronize()
     t_create = time.time() - t0
     # autotune the plan of each orientation on a short candidate list
@@ -780,6 +783,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"rmat{args.scale}-spmm-ksweep", "scale": args.scale, "n": N, "nnz": nnz,
                        "generated_edges": args.edge_factor << args.scale, "ks": ks, "values": "pattern",
+                       "reorder": bool(args.reorder),
                        "l2": "flushed (512 MB write) before every step; inputs > L2",
                        "parallelism": "replicas" if world > 1 else "single"},
             "per_k": breakdown,

@@ -53,6 +53,7 @@ typedef enum {
 /* create flags */
 #define SPMM_WANT_TRANSPOSE 0x1u   /* also build the transposed (CSC) copy for A^T X */
 #define SPMM_HOST_STREAMING 0x2u   /* keep A in host memory and stream it per call (A X only) */
+#define SPMM_REORDER 0x4u          /* relabel columns by decreasing degree (see spmm_create_csr) */
 
 /* Tuning knobs of the warp-task plan (the GPU form of the paper's tile-row
  * batches, Section 3.4); a NULL pointer or a zero field selects the default.
@@ -117,13 +118,26 @@ typedef struct {
  *   col_idx    nnz int32, 0 <= col < n_cols (any order within a row)
  *   values     nnz values of type vtype, or NULL for a pattern matrix (all 1)
  *   vtype      SPMM_F32, SPMM_BF16 or SPMM_F16 (ignored when values is NULL)
- *   flags      SPMM_WANT_TRANSPOSE, SPMM_HOST_STREAMING or 0
+ *   flags      SPMM_WANT_TRANSPOSE, SPMM_HOST_STREAMING, SPMM_REORDER (or'd), or 0
  *   opts       tuning knobs or NULL
  *   stream     stream for the copies; the call returns after they finish
  * Errors: SPMM_ERR_ARG (null/shape), SPMM_ERR_FORMAT (row_ptr not monotone,
  * wrong row_ptr[0] or row_ptr[n_rows], column out of range), SPMM_ERR_OOM,
- * SPMM_ERR_UNSUPPORTED (streaming with SPMM_WANT_TRANSPOSE), SPMM_ERR_CUDA.
- * The input arrays are copied; the caller keeps ownership.
+ * SPMM_ERR_UNSUPPORTED (streaming with SPMM_WANT_TRANSPOSE or SPMM_REORDER),
+ * SPMM_ERR_CUDA.  The input arrays are copied; the caller keeps ownership.
+ *
+ * SPMM_REORDER (Section 5.1: the vertex order decides how well gathered rows
+ * stay in cache): each orientation's columns are relabelled by decreasing
+ * number of stored entries (ties in index order) inside the handle, so the
+ * most-gathered rows of X share cache lines.  Callers still pass X and get Y
+ * in the original order: every apply first copies X's rows into the new order
+ * (one gather pass over X into a buffer of n_in * k elements that the handle
+ * keeps and grows; growing waits for the device and cannot happen inside a
+ * stream capture).  Rows and the entry order within a row are unchanged, so
+ * results are bit-identical to a handle without the flag given the same X as
+ * a contiguous (ldx = k), 16-byte-aligned array -- the layout of the
+ * relabelled copy.  A strided or misaligned X can give another summation
+ * order (the kernel's vector width follows X's alignment).
  *
  * Streaming mode (SPMM_HOST_STREAMING; Section 3.1 keeps the sparse matrix
  * outside memory and streams it while the dense matrices stay resident, and

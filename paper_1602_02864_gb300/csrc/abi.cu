@@ -47,6 +47,7 @@ static void free_dev(DevCSR& d) {
     cudaFree(d.splits);
     cudaFree(d.partials);
     cudaFree(d.partials_comp);
+    cudaFree(d.perm);
     d = DevCSR{};
 }
 
@@ -65,9 +66,11 @@ static cudaError_t upload(T** dst, const T* src, size_t count, size_t pad, cudaS
 }
 
 // Copy one orientation (host CSR) and its plan to the device.
+// With `reorder`, the columns are relabelled by decreasing count of stored
+// entries (the device keeps the original index of each new label).
 static int build_orientation(DevCSR& d, int64_t n_rows, int64_t n_cols, const int64_t* row_ptr,
                              const int32_t* col_idx, const void* val, size_t vsize, const Params& p,
-                             cudaStream_t s, int64_t* bytes) {
+                             bool reorder, cudaStream_t s, int64_t* bytes) {
     d.n_rows = n_rows;
     d.n_cols = n_cols;
     d.nnz = row_ptr[n_rows];
@@ -75,7 +78,22 @@ static int build_orientation(DevCSR& d, int64_t n_rows, int64_t n_cols, const in
     cudaError_t e;
     if ((e = upload(&d.row_ptr, row_ptr, (size_t)n_rows + 1, 2, s, bytes)) != cudaSuccess)
         return cuda_fail(e, "row_ptr");
-    if ((e = upload(&d.col_idx, col_idx, (size_t)d.nnz, 8, s, bytes)) != cudaSuccess) return cuda_fail(e, "col_idx");
+    if (reorder) {
+        std::vector<int32_t> old_of_new, relabelled;
+        try {
+            relabel_by_degree(n_cols, col_idx, d.nnz, old_of_new, relabelled);
+        } catch (const std::bad_alloc&) {
+            set_error("create: out of host memory for the column relabelling");
+            return SPMM_ERR_OOM;
+        }
+        if ((e = upload(&d.col_idx, relabelled.data(), (size_t)d.nnz, 8, s, bytes)) != cudaSuccess ||
+            (e = upload(&d.perm, old_of_new.data(), (size_t)n_cols, 0, s, bytes)) != cudaSuccess)
+            return cuda_fail(e, "col_idx");
+        // the host vectors are freed on return: finish their copies first
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "col_idx");
+    } else if ((e = upload(&d.col_idx, col_idx, (size_t)d.nnz, 8, s, bytes)) != cudaSuccess) {
+        return cuda_fail(e, "col_idx");
+    }
     if (val) {
         if ((e = upload((char**)&d.val, (const char*)val, (size_t)d.nnz * vsize, 8 * vsize, s, bytes)) != cudaSuccess)
             return cuda_fail(e, "values");
@@ -190,11 +208,16 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
         return SPMM_ERR_ARG;
     }
     if (!row_ptr || (nnz > 0 && !col_idx)) { set_error(w + ": row_ptr/col_idx is NULL"); return SPMM_ERR_ARG; }
-    if (flags & ~(SPMM_WANT_TRANSPOSE | SPMM_HOST_STREAMING)) { set_error(w + ": unknown flag bits"); return SPMM_ERR_ARG; }
-    if ((flags & SPMM_HOST_STREAMING) && (flags & SPMM_WANT_TRANSPOSE)) {
-        set_error(w + ": the streaming mode computes A X only (no SPMM_WANT_TRANSPOSE)");
+    if (flags & ~(SPMM_WANT_TRANSPOSE | SPMM_HOST_STREAMING | SPMM_REORDER)) {
+        set_error(w + ": unknown flag bits");
+        return SPMM_ERR_ARG;
+    }
+    if ((flags & SPMM_HOST_STREAMING) && (flags & (SPMM_WANT_TRANSPOSE | SPMM_REORDER))) {
+        set_error(w + ": the streaming mode computes A X only, without relabelling "
+                      "(no SPMM_WANT_TRANSPOSE or SPMM_REORDER)");
         return SPMM_ERR_UNSUPPORTED;
     }
+    const bool reorder = (flags & SPMM_REORDER) != 0;
     size_t vsize = 0;
     if (values) {
         if (vtype != SPMM_F32 && vtype != SPMM_BF16 && vtype != SPMM_F16) {
@@ -254,7 +277,8 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
         *out = A;
         return SPMM_OK;
     }
-    rc = build_orientation(A->fwd, n_rows, n_cols, row_ptr, col_idx, values, vsize, prm, s, &A->device_bytes);
+    rc = build_orientation(A->fwd, n_rows, n_cols, row_ptr, col_idx, values, vsize, prm, reorder, s,
+                           &A->device_bytes);
     if (rc == SPMM_OK && (flags & SPMM_WANT_TRANSPOSE)) {
         // CSR of A^T by a stable counting sort on the column index.
         std::vector<int64_t> tptr((size_t)n_cols + 1, 0);
@@ -278,7 +302,7 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
                     if (values) std::memcpy(&tval[(size_t)q * vsize], (const char*)values + p * vsize, vsize);
                 }
             rc = build_orientation(A->tr, n_cols, n_rows, tptr.data(), tidx.data(), values ? tval.data() : nullptr,
-                                   vsize, prm, s, &A->device_bytes);
+                                   vsize, prm, reorder, s, &A->device_bytes);
             A->has_tr = (rc == SPMM_OK);
         }
     }
@@ -444,6 +468,13 @@ int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int3
         set_error("spmm_apply: 16-bit values need X of the same 16-bit type (or use F32 values)");
         return SPMM_ERR_UNSUPPORTED;
     }
+    if (d.perm) {   // relabelled columns: gather X's rows into the new order first
+        const void* Xp = nullptr;
+        const int rc = reorder_x(const_cast<spmm_mat*>(A), d, X, ldx, k, xtype, s, &Xp);
+        if (rc != SPMM_OK) return rc;
+        X = Xp;
+        ldx = k;
+    }
     FwdArgs a;
     int vec = 1, ch = 1;
     set_geometry(a, X, ldx, k, xtype, Y, ldy, &vec, &ch);
@@ -513,6 +544,7 @@ extern "C" int spmm_destroy(spmm_mat_t A) {
     cudaError_t e = cudaDeviceSynchronize();
     if (A->streaming) stream_release(A);
     hostio_release(A);
+    cudaFree(A->xperm);
     free_dev(A->fwd);
     free_dev(A->tr);
     cudaFree(A->status);

@@ -54,6 +54,7 @@ struct DevCSR {
     float* partials = nullptr;      // scratch: n_slots x kSlotStride floats
     float* partials_comp = nullptr; // compensation terms of the partials (compensated plans only)
     int64_t n_slots = 0;
+    int32_t* perm = nullptr;        // SPMM_REORDER: original index of relabelled column c (n_cols)
 };
 
 // Streaming mode: the matrix stays in (pinned) host memory and flows to HBM
@@ -119,6 +120,8 @@ struct spmm_mat {
     bool streaming = false;
     spmm::Streamer st;
     spmm::HostIO hio;
+    void* xperm = nullptr;      // SPMM_REORDER: X with its rows in relabelled order (grow-only)
+    size_t xperm_bytes = 0;
 };
 
 namespace spmm {
@@ -128,6 +131,13 @@ HostPlan build_plan(const int64_t* row_ptr, int64_t n_rows, const Params& p);
 
 // vpart.cu
 void hostio_release(spmm_mat* A);
+
+// reorder.cu
+void relabel_by_degree(int64_t n_cols, const int32_t* col_idx, int64_t nnz, std::vector<int32_t>& old_of_new,
+                       std::vector<int32_t>& relabelled);
+int reorder_reserve(spmm_mat* A, int64_t n_in, int32_t k, int32_t xtype, cudaStream_t s);
+int reorder_x(spmm_mat* A, const DevCSR& d, const void* X, int64_t ldx, int32_t k, int32_t xtype, cudaStream_t s,
+              const void** Xp);
 
 // abi.cu
 void set_error(const std::string& msg);

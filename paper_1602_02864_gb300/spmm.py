@@ -23,6 +23,7 @@ SPMM_ERR_ARG, SPMM_ERR_CUDA, SPMM_ERR_OOM, SPMM_ERR_FORMAT, SPMM_ERR_TIMEOUT, SP
     -1, -2, -3, -4, -5, -6)
 SPMM_WANT_TRANSPOSE = 0x1
 SPMM_HOST_STREAMING = 0x2
+SPMM_REORDER = 0x4
 
 _STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_FORMAT", -5: "ERR_TIMEOUT",
            -6: "ERR_UNSUPPORTED"}
@@ -415,9 +416,10 @@ class SparseMatrix:
     """A sparse matrix resident in HBM: ``SparseMatrix(A_csr).apply(X)``."""
 
     def __init__(self, n_rows, n_cols, row_ptr, col_idx, values=None, transpose=False,
-                 opts: spmm_opts | None = None, stream=None, streaming=False):
+                 opts: spmm_opts | None = None, stream=None, streaming=False, reorder=False):
         self.n_rows, self.n_cols = int(n_rows), int(n_cols)
-        flags = (SPMM_WANT_TRANSPOSE if transpose else 0) | (SPMM_HOST_STREAMING if streaming else 0)
+        flags = ((SPMM_WANT_TRANSPOSE if transpose else 0) | (SPMM_HOST_STREAMING if streaming else 0)
+                 | (SPMM_REORDER if reorder else 0))
         if streaming:
             # the library borrows these host arrays until close(): keep them alive
             self._borrowed = (np.ascontiguousarray(row_ptr, dtype=np.int64),
@@ -436,12 +438,14 @@ class SparseMatrix:
         return self
 
     @classmethod
-    def batched(cls, graphs, transpose=False, weighted=True, opts: spmm_opts | None = None, stream=None):
+    def batched(cls, graphs, transpose=False, weighted=True, opts: spmm_opts | None = None, stream=None,
+                reorder=False):
         """Block-diagonal handle over a list of graphs (one launch per apply)."""
         self = cls.__new__(cls)
         self.n_rows = int(sum(g.n_rows for g in graphs))
         self.n_cols = int(sum(g.n_cols for g in graphs))
-        self.handle = spmm_create_batched(graphs, SPMM_WANT_TRANSPOSE if transpose else 0, opts, stream, weighted)
+        flags = (SPMM_WANT_TRANSPOSE if transpose else 0) | (SPMM_REORDER if reorder else 0)
+        self.handle = spmm_create_batched(graphs, flags, opts, stream, weighted)
         return self
 
     def apply_host(self, X, Y, transpose=False, group_cols=0, budget_bytes=0, stream=None) -> int:

@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--pagerank-iters", type=int, default=30)
     ap.add_argument("--workload", default="ksweep",
-                    choices=["ksweep", "streaming", "nmf-batched", "eigs", "gather-ceiling", "vpart"],
+                    choices=["ksweep", "streaming", "nmf-batched", "eigs", "gather-ceiling", "vpart", "ordering"],
                     help="ksweep: the headline SpMM sweep + PageRank; the others measure the streaming mode, "
                          "the batched launch with NMF and the eigensolver")
     return ap.parse_args()
@@ -389,6 +389,70 @@ def workload_vpart(args):
                       "setup_s": {"generate": round(t_gen, 1)}})
 
 
+def workload_ordering(args):
+    """Vertex-ordering study (Section 5.1, stochastic block model figure): SpMM
+    at k = 1 and 8 on graphs of 2^scale vertices and average degree 16 --
+    R-MAT in natural and randomly permuted order, and SBM graphs with 16 or
+    1024 clusters and 50% or 90% of edges inside clusters, in clustered and
+    randomly permuted (unclustered) order.  Each graph runs resident in HBM
+    (the paper's in-memory case) and streamed from pinned host memory (its
+    semi-external analogue); the L2 is flushed before each timed call."""
+    import torch
+    import oracle
+    from paper_1602_02864_gb300 import spmm
+    N = 1 << args.scale
+    deg = args.edge_factor
+    specs = [("rmat", None, None, False), ("rmat", None, None, True)]
+    for C in (16, 1024):
+        for p_in in (0.5, 0.9):
+            for perm in (False, True):
+                specs.append(("sbm", C, p_in, perm))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    X = {k: torch.from_numpy(synth.dense(N, k, seed=0)).cuda() for k in (1, 8)}
+    Y = {k: torch.empty((N, k), device="cuda") for k in (1, 8)}
+    rows = np.unique(synth.sample_rows(N, 2000, seed=9))
+    Xh8 = X[8].cpu().numpy()
+    out = []
+    for kind, C, p_in, perm in specs:
+        if kind == "rmat":
+            A = synth.rmat_permuted_csr(args.scale, deg * N) if perm else synth.rmat_csr(args.scale, deg * N)
+            name = "rmat-" + ("permuted" if perm else "natural")
+        else:
+            A = synth.sbm_csr(N, C, deg, p_in, seed=0, permuted=perm)
+            name = f"sbm-C{C}-in{int(p_in * 100)}-" + ("unclustered" if perm else "clustered")
+        entry = {"graph": name, "nnz": A.nnz}
+        for mode in ("resident", "streaming"):
+            h = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, streaming=(mode == "streaming"))
+            for k in (1, 8):
+                for _ in range(2):
+                    h.apply(X[k], Y=Y[k])
+                ts = []
+                for _ in range(args.steps):
+                    flush.zero_()
+                    ts.append(event_ms(lambda: h.apply(X[k], Y=Y[k]), 1))
+                ms = statistics.median(ts)
+                entry[f"{mode}_k{k}_ms"] = round(ms, 4)
+                entry[f"{mode}_k{k}_nnz_per_s"] = A.nnz / (ms / 1e3)
+            if mode == "resident":
+                ref = oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xh8, rows, threads=oracle.num_threads())
+                scl = oracle.spmm_rows(A.row_ptr, A.col_idx, None, np.abs(Xh8), rows, threads=oracle.num_threads())
+                got = Y[8][torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+                entry["sampled_max_err_over_absprod"] = float((np.abs(got - ref) / np.maximum(scl, 1e-300)).max())
+            h.sync_status()
+            h.close()
+        for k in (1, 8):
+            entry[f"sem_over_im_k{k}"] = entry[f"resident_k{k}_ms"] / entry[f"streaming_k{k}_ms"]
+        out.append(entry)
+        del A
+    nat = out[0]
+    return base_line(args, f"vertex-ordering study, SpMM k=1 nonzeros/s on R-MAT and SBM graphs "
+                           f"(2^{args.scale} vertices, avg degree {deg})",
+                     nat["resident_k1_nnz_per_s"], "nnz/s", nat["resident_k1_ms"],
+                     f"ordering-{args.scale}", "f32",
+                     {"graphs": out, "l2": "flushed before each timed call",
+                      "timing": "median of --steps calls, CUDA events"})
+
+
 def workload_nmf_batched(args):
     """256 Chung-Lu graphs in one block-diagonal handle: batched SpMM vs one
     launch per graph, then NMF (k = 8, 16, 32; 50 steps; FP32 and BF16)."""
@@ -527,7 +591,8 @@ def main():
         import torch
         torch.cuda.set_device(local)
         fn = {"streaming": workload_streaming, "nmf-batched": workload_nmf_batched, "eigs": workload_eigs,
-              "gather-ceiling": workload_gather_ceiling, "vpart": workload_vpart}
+              "gather-ceiling": workload_gather_ceiling, "vpart": workload_vpart,
+              "ordering": workload_ordering}
         print(json.dumps(fn[args.workload](args)), flush=True)
         return
 

@@ -10,6 +10,9 @@ a/b/c/d = 0.57/0.19/0.19/0.05):
 * ``rmat_csr(scale, n_edges)``: R-MAT edges, duplicates merged, self-loops kept.
 * ``chunglu_csr(g)``: graph ``g`` of a batch of Chung-Lu power-law graphs
   (exponent 2.1, size log-uniform in [1e3, 2e5], average degree U[8, 32]).
+* ``sbm_csr(n, clusters, avg_deg, p_in, permuted)``: stochastic block model,
+  clustered ids or a seeded random relabelling (Section 5.1's ordering study).
+* ``rmat_permuted_csr(scale)``: R-MAT with randomly relabelled vertices.
 * ``sym_rmat_csr(scale)``: symmetrised R-MAT (8*N directed edges, union with the
   transpose), lognormal(0,1) pair weights, normalised D^-1/2 A D^-1/2.
 """
@@ -61,6 +64,9 @@ def _load():
             lib.synth_chunglu_edges.argtypes = [u64, i64, i64, i64, f64, P, P]
             lib.synth_chunglu_edges.restype = i32
             lib.synth_sym_lognormal.argtypes = [u64, i64, P, P, i32, P]
+            lib.synth_permutation.argtypes = [u64, i64, P]
+            lib.synth_relabel_edges.argtypes = [i64, P, P, P]
+            lib.synth_sbm_edges.argtypes = [u64, i64, i64, i64, f64, P, P]
             _lib = lib
     return _lib
 
@@ -196,6 +202,51 @@ def sample_rows(n_rows: int, n: int, seed: int = 0) -> np.ndarray:
     out = np.empty(n, dtype=np.int64)
     _load().synth_sample_rows(seed, n_rows, n, _p(out))
     return out
+
+
+def permutation(n: int, seed: int = 0) -> np.ndarray:
+    """A seeded uniform random permutation of 0..n-1 (uint32)."""
+    out = np.empty(n, dtype=np.uint32)
+    _load().synth_permutation(seed, n, _p(out))
+    return out
+
+
+def relabel_edges(src, dst, perm) -> None:
+    """Map both endpoints of an edge list through perm, in place."""
+    assert src.dtype == np.uint32 and dst.dtype == np.uint32 and perm.dtype == np.uint32
+    _load().synth_relabel_edges(len(src), _p(src), _p(dst), _p(np.ascontiguousarray(perm)))
+
+
+def sbm_edges(n: int, n_clusters: int, m: int, p_in: float, seed: int = 0):
+    """Stochastic block model edge list: equal clusters of consecutive ids,
+    uniform sources, destination inside the source's cluster with probability
+    p_in, else uniform outside it."""
+    src = np.empty(m, dtype=np.uint32)
+    dst = np.empty(m, dtype=np.uint32)
+    _load().synth_sbm_edges(seed, n, n_clusters, m, p_in, _p(src), _p(dst))
+    return src, dst
+
+
+def sbm_csr(n: int, n_clusters: int, avg_deg: float, p_in: float, seed: int = 0, permuted: bool = False) -> CSR:
+    """SBM graph in CSR (duplicates merged); clustered ids, or ids relabelled
+    by a seeded uniform permutation (the unclustered order)."""
+    src, dst = sbm_edges(n, n_clusters, int(round(n * avg_deg)), p_in, seed)
+    if permuted:
+        relabel_edges(src, dst, permutation(n, seed=seed + 1))
+    A = edges_to_csr(n, n, src, dst)
+    del src, dst
+    return A
+
+
+def rmat_permuted_csr(scale: int, n_edges: int | None = None, seed: int = 0) -> CSR:
+    """R-MAT graph with its vertex ids relabelled by a seeded uniform permutation
+    (hubs no longer sit at low ids)."""
+    n = 1 << scale
+    src, dst = rmat_edges(scale, 16 * n if n_edges is None else n_edges, seed)
+    relabel_edges(src, dst, permutation(n, seed=seed + 1))
+    A = edges_to_csr(n, n, src, dst)
+    del src, dst
+    return A
 
 
 def largest_component(A: CSR) -> CSR:

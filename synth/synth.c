@@ -16,6 +16,10 @@
  *     every level draws one quadrant, no noise, no vertex permutation.
  *   - Chung-Lu power-law graphs (expected degree proportional to
  *     (i+1)^(-1/(gamma-1))), destinations relabelled by a seeded permutation.
+ *   - stochastic block model graphs (Section 5.1's ordering experiment):
+ *     equal clusters of consecutive ids, sources uniform, a destination in
+ *     the source's cluster with probability p_in, else uniform outside it;
+ *     any graph can be relabelled by a seeded uniform permutation.
  *   - the symmetrised union A + A^T with one lognormal(0,1) weight per
  *     unordered pair and symmetric degree normalisation D^-1/2 A D^-1/2.
  * Edge lists become CSR by a stable LSD radix sort on (row, col) keys and a
@@ -64,7 +68,9 @@ enum {
     DOM_PERM = 0x5045524du,  /* permutations                       */
     DOM_LOGN = 0x4c4f474eu,  /* lognormal pair weights             */
     DOM_SIZE = 0x53495a45u,  /* per-graph size / degree draws      */
-    DOM_SAMP = 0x53414d50u   /* sampled row ids                    */
+    DOM_SAMP = 0x53414d50u,  /* sampled row ids                    */
+    DOM_VPRM = 0x5650524du,  /* vertex relabelling permutations    */
+    DOM_SBM  = 0x53424d45u   /* stochastic block model edges       */
 };
 
 static inline void draw4(uint64_t seed, uint64_t seed2, uint64_t idx, uint32_t sub,
@@ -328,4 +334,62 @@ void synth_sym_lognormal(uint64_t seed, int64_t n, const int64_t* row_ptr, const
         }
     free(w);
     free(deg);
+}
+
+/* ------------------------------------------------- vertex relabelling -- */
+/* A uniform random permutation of 0..n-1 (Fisher-Yates; position i draws its
+ * partner from 53-bit uniforms of its own counter). */
+void synth_permutation(uint64_t seed, int64_t n, uint32_t* perm) {
+    for (int64_t i = 0; i < n; ++i) perm[i] = (uint32_t)i;
+    for (int64_t i = n - 1; i > 0; --i) {
+        uint32_t w[4];
+        draw4(seed, 0, (uint64_t)i, 0, DOM_VPRM, w);
+        int64_t j = (int64_t)(u53(w[0], w[1]) * (double)(i + 1));
+        if (j > i) j = i;
+        uint32_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+    }
+}
+
+/* Map both endpoints of m edges through perm, in place. */
+void synth_relabel_edges(int64_t m, uint32_t* src, uint32_t* dst, const uint32_t* perm) {
+    #pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < m; ++e) {
+        src[e] = perm[src[e]];
+        dst[e] = perm[dst[e]];
+    }
+}
+
+/* ------------------------------------------------ stochastic block model -- */
+/* n vertices in n_clusters equal clusters of consecutive ids (cluster of v is
+ * v * n_clusters / n); edge e: source uniform over all vertices; with
+ * probability p_in the destination is uniform over the source's cluster,
+ * otherwise uniform over the vertices outside it.  Self-loops can occur
+ * inside a cluster. */
+void synth_sbm_edges(uint64_t seed, int64_t n, int64_t n_clusters, int64_t m, double p_in, uint32_t* src,
+                     uint32_t* dst) {
+    #pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < m; ++e) {
+        uint32_t w[4], v[4];
+        draw4(seed, 0, (uint64_t)e, 0, DOM_SBM, w);
+        draw4(seed, 0, (uint64_t)e, 1, DOM_SBM, v);
+        int64_t s = (int64_t)(u53(w[0], w[1]) * (double)n);
+        if (s >= n) s = n - 1;
+        const int64_t c = s * n_clusters / n;
+        /* cluster c holds the ids v with v * n_clusters / n == c */
+        const int64_t c0 = (c * n + n_clusters - 1) / n_clusters;
+        const int64_t c1 = ((c + 1) * n + n_clusters - 1) / n_clusters;
+        const double u = u53(w[2], w[3]);
+        int64_t d;
+        if (u < p_in) {
+            d = c0 + (int64_t)(u53(v[0], v[1]) * (double)(c1 - c0));
+            if (d >= c1) d = c1 - 1;
+        } else {
+            const int64_t outside = n - (c1 - c0);
+            int64_t t = (int64_t)(u53(v[0], v[1]) * (double)outside);
+            if (t >= outside) t = outside - 1;
+            d = t < c0 ? t : t + (c1 - c0);
+        }
+        src[e] = (uint32_t)s;
+        dst[e] = (uint32_t)d;
+    }
 }

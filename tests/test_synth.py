@@ -79,3 +79,57 @@ def test_chunglu_batch_sizes():
     assert 0.5 * d * n < A.nnz <= d * n + 1
     deg = A.degrees()
     assert deg.max() > 20 * deg.mean()       # heavy tail
+
+
+# ---- vertex relabelling and the stochastic block model (ordering study)
+
+def test_permutation_is_uniform_bijection():
+    for n in (1, 2, 10, 1000):
+        p = synth.permutation(n, seed=4)
+        assert np.array_equal(np.sort(p), np.arange(n))
+    assert np.array_equal(synth.permutation(50, seed=1), synth.permutation(50, seed=1))
+    assert not np.array_equal(synth.permutation(50, seed=1), synth.permutation(50, seed=2))
+    # all 3! orders equally likely (an off-by-one in Fisher-Yates skews this)
+    counts = {}
+    trials = 6000
+    for s in range(trials):
+        key = tuple(synth.permutation(3, seed=s))
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == 6
+    exp = trials / 6
+    sd = np.sqrt(trials * (1 / 6) * (5 / 6))
+    assert all(abs(c - exp) < 5 * sd for c in counts.values()), counts
+
+
+@pytest.mark.parametrize("n,C,p_in", [(1 << 14, 16, 0.9), (10007, 7, 0.5), (5000, 1, 1.0), (4096, 64, 0.0)])
+def test_sbm_inside_fraction_and_clusters(n, C, p_in):
+    m = 200_000
+    src, dst = synth.sbm_edges(n, C, m, p_in, seed=3)
+    assert src.max() < n and dst.max() < n
+    cs = src.astype(np.int64) * C // n
+    cd = dst.astype(np.int64) * C // n
+    inside = (cs == cd).mean()
+    if C == 1:
+        assert inside == 1.0
+    else:
+        sd = np.sqrt(p_in * (1 - p_in) / m)
+        assert abs(inside - p_in) <= 5 * sd + 1e-12, (inside, p_in)
+    # sources uniform over the vertices: cluster shares match cluster sizes
+    sizes = np.bincount(np.arange(n) * C // n, minlength=C)
+    share = np.bincount(cs, minlength=C) / m
+    assert np.all(np.abs(share - sizes / n) < 5 * np.sqrt(sizes / n / m) + 1e-12)
+
+
+def test_relabelling_preserves_degrees():
+    A = synth.sbm_csr(1 << 13, 8, 12, 0.8, seed=2)
+    B = synth.sbm_csr(1 << 13, 8, 12, 0.8, seed=2, permuted=True)
+    assert A.nnz == B.nnz
+    assert np.array_equal(np.sort(np.diff(A.row_ptr)), np.sort(np.diff(B.row_ptr)))
+    assert np.array_equal(np.sort(np.bincount(A.col_idx, minlength=A.n_cols)),
+                          np.sort(np.bincount(B.col_idx, minlength=B.n_cols)))
+    R = synth.rmat_csr(12, seed=5)
+    P = synth.rmat_permuted_csr(12, seed=5)
+    assert R.nnz == P.nnz
+    assert np.array_equal(np.sort(np.diff(R.row_ptr)), np.sort(np.diff(P.row_ptr)))
+    # the permutation moves the hubs away from the low ids
+    assert np.diff(R.row_ptr)[:16].sum() > 4 * np.diff(P.row_ptr)[:16].sum()

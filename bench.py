@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--pagerank-iters", type=int, default=30)
     ap.add_argument("--workload", default="ksweep",
-                    choices=["ksweep", "streaming", "nmf-batched", "eigs", "gather-ceiling", "vpart", "ordering"],
+                    choices=["ksweep", "streaming", "nmf-batched", "eigs", "gather-ceiling", "vpart", "ordering",
+                             "file"],
                     help="ksweep: the headline SpMM sweep + PageRank; the others measure the streaming mode, "
                          "the batched launch with NMF and the eigensolver")
     return ap.parse_args()
@@ -453,6 +454,88 @@ def workload_ordering(args):
                       "timing": "median of --steps calls, CUDA events"})
 
 
+def _fs_type(path):
+    """File-system type of the mount holding path (from /proc/mounts)."""
+    best, fs = "", "unknown"
+    try:
+        real = os.path.realpath(path)
+        with open("/proc/mounts") as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 3 and real.startswith(parts[1]) and len(parts[1]) > len(best):
+                    best, fs = parts[1], parts[2]
+    except OSError:
+        pass
+    return fs
+
+
+def workload_file(args):
+    """Semi-external SpMM (Section 3.1): the matrix in a file on the local file
+    system, read on every apply (page cache and O_DIRECT), against the same
+    matrix streamed from pinned host memory and resident in HBM; k = 1 and 8."""
+    import tempfile
+    import torch
+    import oracle
+    from paper_1602_02864_gb300 import spmm
+    N = 1 << args.scale
+    A = synth.rmat_csr(args.scale, args.edge_factor * N, seed=0)
+    nnz = A.nnz
+    d = tempfile.mkdtemp(prefix="spmm_file_")
+    path = os.path.join(d, "a.spmm")
+    t = time.time()
+    spmm.spmm_write_csr_file(path, A)
+    t_write = time.time() - t
+    file_bytes = os.path.getsize(path)
+    X = {k: torch.from_numpy(synth.dense(N, k, seed=0)).cuda() for k in (1, 8)}
+    Y = {k: torch.empty((N, k), device="cuda") for k in (1, 8)}
+    res = {"fs": _fs_type(d), "file_GB": file_bytes / 1e9, "write_s": round(t_write, 2)}
+    handles = [("resident", lambda: spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None)),
+               ("host_streaming", lambda: spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, streaming=True)),
+               ("file_buffered", lambda: spmm.SparseMatrix.from_file(path, N, N)),
+               ("file_direct", lambda: spmm.SparseMatrix.from_file(path, N, N, direct=True))]
+    ref = None
+    rows = np.unique(synth.sample_rows(N, 2000, seed=3))
+    for name, make in handles:
+        try:
+            h = make()
+        except spmm.SpmmError as e:
+            res[name] = {"unavailable": str(e)[:160]}
+            continue
+        entry = {}
+        for k in (1, 8):
+            h.apply(X[k], Y=Y[k])
+            ts = []
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                h.apply(X[k], Y=Y[k])
+                torch.cuda.synchronize()
+                ts.append((time.perf_counter() - t0) * 1e3)
+            ms = statistics.median(ts)
+            entry[f"k{k}_ms"] = round(ms, 3)
+            entry[f"k{k}_nnz_per_s"] = nnz / (ms / 1e3)
+            entry[f"k{k}_matrix_GBps"] = (nnz * 4 + (N + 1) * 8) / (ms / 1e3) / 1e9
+        got = Y[8][torch.from_numpy(rows).cuda()].cpu().numpy()
+        if ref is None:
+            ref = got
+        entry["identical_to_resident"] = bool(np.array_equal(got, ref))
+        h.sync_status()
+        h.close()
+        res[name] = entry
+    Xh = X[8].cpu().numpy()
+    o = oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xh, rows, threads=oracle.num_threads())
+    scl = oracle.spmm_rows(A.row_ptr, A.col_idx, None, np.abs(Xh), rows, threads=oracle.num_threads())
+    res["sampled_max_err_over_absprod"] = float((np.abs(ref - o) / np.maximum(scl, 1e-300)).max())
+    os.unlink(path)
+    os.rmdir(d)
+    best = res.get("file_direct", {}) if "k1_ms" in res.get("file_direct", {}) else res["file_buffered"]
+    return base_line(args, f"semi-external SpMM nonzeros/s, R-MAT scale {args.scale} matrix read from a file "
+                           f"per apply (k=1)", best["k1_nnz_per_s"], "nnz/s", best["k1_ms"],
+                     f"rmat{args.scale}-file", "f32",
+                     {"modes": res, "n": N, "nnz": nnz,
+                      "timing": "wall clock per apply incl. the file reads (median of --steps)"})
+
+
 def workload_nmf_batched(args):
     """256 Chung-Lu graphs in one block-diagonal handle: batched SpMM vs one
     launch per graph, then NMF (k = 8, 16, 32; 50 steps; FP32 and BF16)."""
@@ -592,7 +675,7 @@ def main():
         torch.cuda.set_device(local)
         fn = {"streaming": workload_streaming, "nmf-batched": workload_nmf_batched, "eigs": workload_eigs,
               "gather-ceiling": workload_gather_ceiling, "vpart": workload_vpart,
-              "ordering": workload_ordering}
+              "ordering": workload_ordering, "file": workload_file}
         print(json.dumps(fn[args.workload](args)), flush=True)
         return
 

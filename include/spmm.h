@@ -47,13 +47,15 @@ typedef enum {
     SPMM_ERR_OOM = -3,          /* device or host allocation failed                      */
     SPMM_ERR_FORMAT = -4,       /* the sparse matrix is malformed                        */
     SPMM_ERR_TIMEOUT = -5,      /* a bounded device-side wait ran out                    */
-    SPMM_ERR_UNSUPPORTED = -6   /* a valid but unimplemented combination                 */
+    SPMM_ERR_UNSUPPORTED = -6,  /* a valid but unimplemented combination                 */
+    SPMM_ERR_IO = -7            /* a file could not be opened, read or written           */
 } spmm_status;
 
 /* create flags */
 #define SPMM_WANT_TRANSPOSE 0x1u   /* also build the transposed (CSC) copy for A^T X */
 #define SPMM_HOST_STREAMING 0x2u   /* keep A in host memory and stream it per call (A X only) */
 #define SPMM_REORDER 0x4u          /* relabel columns by decreasing degree (see spmm_create_csr) */
+#define SPMM_FILE_DIRECT 0x8u      /* spmm_create_file: read with O_DIRECT (bypass the page cache) */
 
 /* Tuning knobs of the warp-task plan (the GPU form of the paper's tile-row
  * batches, Section 3.4); a NULL pointer or a zero field selects the default.
@@ -236,6 +238,43 @@ int spmm_apply(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype x
  * paper operation: the failure-detection side of the asynchronous staging.
  */
 int spmm_sync_status(spmm_mat_t A, void* stream);
+
+/*
+ * spmm_write_csr_file -- host-only: write a CSR matrix to `path` in the
+ * library's file layout (the sparse matrix on storage, Section 3.1): a
+ * 4096-byte header ("SPMMCSR1", int64 n_rows, n_cols, nnz, int32 vtype (-1 for
+ * a pattern matrix), int32 0, int64 offsets of the three sections), then
+ * int64 row_ptr[n_rows+1], int32 col_idx[nnz] and the values, each section
+ * starting on a 4096-byte boundary.  Written to a temporary name and renamed.
+ * Validates like spmm_create_csr.  Errors: SPMM_ERR_ARG, SPMM_ERR_FORMAT,
+ * SPMM_ERR_IO.
+ */
+int spmm_write_csr_file(const char* path, int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t* row_ptr,
+                        const int32_t* col_idx, const void* values, spmm_dtype vtype);
+
+/*
+ * spmm_create_file -- a handle whose matrix stays in a file written by
+ * spmm_write_csr_file: the semi-external mode of Section 3.1 (vertex-sized
+ * data in memory, edge-sized data on storage, streamed for every product).
+ * The row pointers are read once into pinned host memory and the warp-task
+ * plan goes to HBM; every spmm_apply reads the column indices (and values) of
+ * each block of whole tasks from the file with parallel preads into pinned
+ * staging buffers and streams them through two HBM slots as in
+ * SPMM_HOST_STREAMING, so reading block b+1 overlaps copying and multiplying
+ * block b.  Every column index read is range-checked on the host before it
+ * reaches the GPU.
+ *   path    the file (kept open until spmm_destroy; it must not change)
+ *   flags   0 or SPMM_FILE_DIRECT (O_DIRECT reads that bypass the page cache;
+ *           SPMM_ERR_UNSUPPORTED where the file system refuses O_DIRECT)
+ *   opts    tuning knobs or NULL (stream_slot_kib sets the block size)
+ * A X only (no transpose).  spmm_apply on the handle blocks the calling thread
+ * until the last block has been read; the multiplication finishes
+ * asynchronously on the stream.  Errors at create: SPMM_ERR_IO (open/read),
+ * SPMM_ERR_FORMAT (not such a file, bad row pointers), SPMM_ERR_OOM,
+ * SPMM_ERR_CUDA; at apply: SPMM_ERR_IO (a read failed or the file was
+ * truncated), SPMM_ERR_FORMAT (a column index out of range: the file changed).
+ */
+int spmm_create_file(spmm_mat_t* out, const char* path, uint32_t flags, const spmm_opts* opts, void* stream);
 
 /*
  * spmm_vpart_cols -- host-only: the width of the vertical partitions

@@ -6,6 +6,8 @@
 // transposed rows list their entries in increasing original-row order).
 // spmm_apply only launches kernels: it allocates nothing and never
 // synchronises the host.
+#include <unistd.h>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -313,6 +315,77 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
         delete A;
         return rc;
     }
+    *out = A;
+    return SPMM_OK;
+}
+
+extern "C" int spmm_create_file(spmm_mat_t* out, const char* path, uint32_t flags, const spmm_opts* opts,
+                                void* stream) {
+    set_error("");
+    if (!out || !path) { set_error("spmm_create_file: NULL argument"); return SPMM_ERR_ARG; }
+    if (flags & ~SPMM_FILE_DIRECT) {
+        set_error("spmm_create_file: only SPMM_FILE_DIRECT is accepted (A X only, no relabelling)");
+        return SPMM_ERR_UNSUPPORTED;
+    }
+    FileCSR f;
+    int rc = file_open(path, (flags & SPMM_FILE_DIRECT) != 0, &f);
+    if (rc != SPMM_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    spmm_mat* A = new (std::nothrow) spmm_mat();
+    if (!A) {
+        ::close(f.fd);
+        set_error("spmm_create_file: out of host memory");
+        return SPMM_ERR_OOM;
+    }
+    A->params = resolve_params(opts);
+    A->vtype = f.vtype;
+    A->row_off = {0, f.n_rows};
+    A->col_off = {0, f.n_cols};
+    A->a2 = {0.0};
+    A->streaming = true;
+    A->fwd.n_rows = f.n_rows;
+    A->fwd.n_cols = f.n_cols;
+    A->fwd.nnz = f.nnz;
+    A->st.file = f;
+    auto fail = [&](int code) {
+        stream_release(A);   // closes the file
+        free_dev(A->fwd);
+        cudaFree(A->status);
+        delete A;
+        return code;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc((void**)&A->status, sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMemsetAsync(A->status, 0, sizeof(int32_t), s)) != cudaSuccess)
+        return fail(cuda_fail(e, "spmm_create_file: status word"));
+    // row pointers: read once into pinned memory and validated
+    const int64_t rp_bytes = (f.n_rows + 1) * 8;
+    char* rp_buf = nullptr;
+    if ((e = cudaHostAlloc((void**)&rp_buf, (size_t)rp_bytes + 2 * kFileAlign, cudaHostAllocDefault)) != cudaSuccess)
+        return fail(cuda_fail(e, "spmm_create_file: row pointers"));
+    std::string err;
+    const char* rp = file_read_range(f.fd, f.direct, f.off_rp, rp_bytes, rp_buf, 8, 0, &err);
+    if (!rp) {
+        cudaFreeHost(rp_buf);
+        set_error("spmm_create_file: " + err);
+        return fail(SPMM_ERR_IO);
+    }
+    // keep the row pointers at the start of their own pinned buffer
+    if (rp != rp_buf) std::memmove(rp_buf, rp, (size_t)rp_bytes);
+    A->st.h_rp_owned = reinterpret_cast<int64_t*>(rp_buf);
+    const int64_t* row_ptr = A->st.h_rp_owned;
+    if (row_ptr[0] != 0 || row_ptr[f.n_rows] != f.nnz) {
+        set_error("spmm_create_file: row_ptr[0] != 0 or row_ptr[n_rows] != nnz");
+        return fail(SPMM_ERR_FORMAT);
+    }
+    for (int64_t i = 0; i < f.n_rows; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) {
+            set_error("spmm_create_file: row_ptr decreases at row " + std::to_string(i));
+            return fail(SPMM_ERR_FORMAT);
+        }
+    const size_t vsize = f.vtype < 0 ? 0 : dtype_size((spmm_dtype)f.vtype);
+    if ((rc = stream_setup(A, row_ptr, nullptr, nullptr, vsize, s)) != SPMM_OK) return fail(rc);
+    if ((rc = stream_file_setup(A, s)) != SPMM_OK) return fail(rc);
     *out = A;
     return SPMM_OK;
 }

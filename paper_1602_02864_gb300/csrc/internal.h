@@ -65,6 +65,16 @@ struct StreamBlock {
     int64_t r0, r1;     // row-pointer range copied (r0 aligned down to 2)
 };
 
+// A CSR file opened by spmm_create_file (layout in filecsr.cpp).
+constexpr int64_t kFileAlign = 4096;
+struct FileCSR {
+    int fd = -1;
+    bool direct = false;               // opened with O_DIRECT
+    int64_t n_rows = 0, n_cols = 0, nnz = 0;
+    int32_t vtype = -1;
+    int64_t off_rp = 0, off_ci = 0, off_val = 0;
+};
+
 struct Streamer {
     const int64_t* h_row_ptr = nullptr;
     const int32_t* h_col_idx = nullptr;
@@ -79,6 +89,13 @@ struct Streamer {
     cudaEvent_t copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
     int32_t fail_block = 0;                // test hook: 1 + block before which a copy "fails"
     int64_t bytes_per_apply = 0;           // host bytes streamed per call
+    // file source (spmm_create_file): blocks are read into pinned staging first
+    FileCSR file;
+    int64_t* h_rp_owned = nullptr;         // pinned row pointers read from the file
+    char* stage_col[2] = {nullptr, nullptr};
+    char* stage_val[2] = {nullptr, nullptr};
+    cudaEvent_t staged[2] = {nullptr, nullptr};   // the copies out of staging buffer i are done
+    int32_t readers = 8;                   // parallel preads per block
 };
 
 struct Params {
@@ -131,6 +148,14 @@ HostPlan build_plan(const int64_t* row_ptr, int64_t n_rows, const Params& p);
 
 // vpart.cu
 void hostio_release(spmm_mat* A);
+
+// filecsr.cpp
+int file_open(const char* path, bool direct, FileCSR* f);
+const char* file_read_range(int fd, bool direct, int64_t off, int64_t len, char* buf, int threads,
+                            int64_t n_cols_check, std::string* err);
+
+// stream.cu (file source)
+int stream_file_setup(spmm_mat* A, cudaStream_t s);
 
 // reorder.cu
 void relabel_by_degree(int64_t n_cols, const int32_t* col_idx, int64_t nnz, std::vector<int32_t>& old_of_new,

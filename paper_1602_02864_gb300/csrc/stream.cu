@@ -11,8 +11,16 @@
 // on a copy stream while the task kernel works on block b; events order each
 // slot's reuse.  The task list, split table and partials live in HBM as in
 // the resident mode, so results are identical to it.
+//
+// The same pipeline serves a matrix kept in a file (spmm_create_file): each
+// block's column indices and values are first read from the file into one of
+// two pinned staging buffers, and the copy to HBM starts from there.
+#include <unistd.h>
+
 #include <algorithm>
 #include <cstring>
+#include <string>
+#include <thread>
 
 #include "internal.h"
 
@@ -86,13 +94,14 @@ int stream_setup(spmm_mat* A, const int64_t* row_ptr, const int32_t* col_idx, co
         if (r == cudaSuccess) *bytes += (int64_t)b;
         return r;
     };
-    if ((e = pin(row_ptr, (size_t)(n + 1) * 8, &S.reg_rp)) != cudaSuccess) return cuda_fail(e, "streaming: pin row_ptr");
+    if (!S.h_rp_owned && (e = pin(row_ptr, (size_t)(n + 1) * 8, &S.reg_rp)) != cudaSuccess)
+        return cuda_fail(e, "streaming: pin row_ptr");
     if ((e = pin(col_idx, (size_t)nnz * 4, &S.reg_ci)) != cudaSuccess) return cuda_fail(e, "streaming: pin col_idx");
     if ((e = pin(values, (size_t)nnz * vsize, &S.reg_val)) != cudaSuccess) return cuda_fail(e, "streaming: pin values");
     for (int i = 0; i < 2; ++i) {
         if ((e = dmalloc((void**)&S.slot_col[i], (size_t)S.slot_nnz * 4)) != cudaSuccess ||
             (e = dmalloc((void**)&S.slot_rp[i], (size_t)S.slot_rows * 8)) != cudaSuccess ||
-            (values && (e = dmalloc(&S.slot_val[i], (size_t)S.slot_nnz * vsize)) != cudaSuccess))
+            (vsize > 0 && (e = dmalloc(&S.slot_val[i], (size_t)S.slot_nnz * vsize)) != cudaSuccess))
             return cuda_fail(e, "streaming: staging slots");
     }
     if ((e = cudaStreamCreateWithFlags(&S.copy, cudaStreamNonBlocking)) != cudaSuccess)
@@ -129,8 +138,30 @@ int stream_setup(spmm_mat* A, const int64_t* row_ptr, const int32_t* col_idx, co
             *bytes += (int64_t)d.n_slots * kSlotStride * sizeof(float);
         }
     }
-    S.bytes_per_apply = nnz * 4 + (int64_t)(values ? nnz * vsize : 0) + (n + 1) * 8;
+    S.bytes_per_apply = nnz * 4 + (int64_t)(nnz * vsize) + (n + 1) * 8;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "streaming: set-up");
+    return SPMM_OK;
+}
+
+// File source: pinned staging buffers for one block of column indices and
+// values each (widened to the file alignment at both ends), used in turn.
+int stream_file_setup(spmm_mat* A, cudaStream_t s) {
+    Streamer& S = A->st;
+    const size_t vsize = S.file.vtype < 0 ? 0 : (S.file.vtype == SPMM_F32 ? 4 : 2);
+    cudaError_t e;
+    for (int i = 0; i < 2; ++i) {
+        if ((e = cudaHostAlloc((void**)&S.stage_col[i], (size_t)S.slot_nnz * 4 + 2 * kFileAlign,
+                               cudaHostAllocDefault)) != cudaSuccess ||
+            (vsize && (e = cudaHostAlloc((void**)&S.stage_val[i], (size_t)S.slot_nnz * vsize + 2 * kFileAlign,
+                                         cudaHostAllocDefault)) != cudaSuccess))
+            return cuda_fail(e, "spmm_create_file: staging buffers");
+        if ((e = cudaEventCreateWithFlags(&S.staged[i], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventRecord(S.staged[i], S.copy)) != cudaSuccess)
+            return cuda_fail(e, "spmm_create_file: events");
+    }
+    const int hc = (int)std::thread::hardware_concurrency();
+    S.readers = std::max(1, std::min(16, hc > 0 ? hc : 8));
+    (void)s;
     return SPMM_OK;
 }
 
@@ -164,18 +195,39 @@ int stream_apply(const spmm_mat* A, const void* X, int64_t ldx, int32_t k, int32
             rc = SPMM_ERR_CUDA;
             break;
         }
+        const int32_t* src_col = S.h_col_idx ? S.h_col_idx + b.c0 : nullptr;
+        const char* src_val = S.h_val ? static_cast<const char*>(S.h_val) + b.c0 * vsize : nullptr;
+        if (S.file.fd >= 0) {
+            // read the block from the file into staging buffer `slot` once the
+            // copies out of it (block bi-2) are done; the GPU meanwhile copies
+            // and multiplies block bi-1
+            if ((e = cudaEventSynchronize(S.staged[slot])) != cudaSuccess) break;
+            std::string err;
+            src_col = reinterpret_cast<const int32_t*>(
+                file_read_range(S.file.fd, S.file.direct, S.file.off_ci + b.c0 * 4, (b.c1 - b.c0) * 4,
+                                S.stage_col[slot], S.readers, S.file.n_cols, &err));
+            if (src_col && vmode)
+                src_val = file_read_range(S.file.fd, S.file.direct, S.file.off_val + b.c0 * (int64_t)vsize,
+                                          (b.c1 - b.c0) * (int64_t)vsize, S.stage_val[slot], S.readers, 0, &err);
+            if (!src_col || (vmode && !src_val)) {
+                set_error("spmm_apply (file): block " + std::to_string(bi) + ": " + err);
+                rc = err.rfind("column", 0) == 0 ? SPMM_ERR_FORMAT : SPMM_ERR_IO;
+                break;
+            }
+        }
         // copy block bi into its slot once the kernel that last read the slot is done
         if ((e = cudaStreamWaitEvent(S.copy, S.freed[slot], 0)) != cudaSuccess) break;
-        if ((e = cudaMemcpyAsync(S.slot_col[slot], S.h_col_idx + b.c0, (size_t)(b.c1 - b.c0) * 4,
-                                 cudaMemcpyHostToDevice, S.copy)) != cudaSuccess)
+        if ((e = cudaMemcpyAsync(S.slot_col[slot], src_col, (size_t)(b.c1 - b.c0) * 4, cudaMemcpyHostToDevice,
+                                 S.copy)) != cudaSuccess)
             break;
-        if (vmode && (e = cudaMemcpyAsync(S.slot_val[slot], static_cast<const char*>(S.h_val) + b.c0 * vsize,
-                                          (size_t)(b.c1 - b.c0) * vsize, cudaMemcpyHostToDevice, S.copy)) != cudaSuccess)
+        if (vmode && (e = cudaMemcpyAsync(S.slot_val[slot], src_val, (size_t)(b.c1 - b.c0) * vsize,
+                                          cudaMemcpyHostToDevice, S.copy)) != cudaSuccess)
             break;
         if ((e = cudaMemcpyAsync(S.slot_rp[slot], S.h_row_ptr + b.r0, (size_t)(b.r1 - b.r0) * 8,
                                  cudaMemcpyHostToDevice, S.copy)) != cudaSuccess)
             break;
         if ((e = cudaEventRecord(S.copied[slot], S.copy)) != cudaSuccess) break;
+        if (S.file.fd >= 0 && (e = cudaEventRecord(S.staged[slot], S.copy)) != cudaSuccess) break;
         if ((e = cudaStreamWaitEvent(s, S.copied[slot], 0)) != cudaSuccess) break;
         // rebased views: global index i of the block lives at slot offset i - c0 (or i - r0)
         a.col_idx = S.slot_col[slot] - b.c0;
@@ -211,6 +263,13 @@ void stream_release(spmm_mat* A) {
     if (S.reg_rp) cudaHostUnregister(const_cast<int64_t*>(S.h_row_ptr));
     if (S.reg_ci) cudaHostUnregister(const_cast<int32_t*>(S.h_col_idx));
     if (S.reg_val) cudaHostUnregister(const_cast<void*>(S.h_val));
+    for (int i = 0; i < 2; ++i) {
+        cudaFreeHost(S.stage_col[i]);
+        cudaFreeHost(S.stage_val[i]);
+        if (S.staged[i]) cudaEventDestroy(S.staged[i]);
+    }
+    cudaFreeHost(S.h_rp_owned);
+    if (S.file.fd >= 0) ::close(S.file.fd);
     S = Streamer{};
 }
 

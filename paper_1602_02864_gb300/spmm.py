@@ -21,12 +21,14 @@ SPMM_F32, SPMM_BF16, SPMM_F16, SPMM_F64 = 0, 1, 2, 3
 SPMM_OK = 0
 SPMM_ERR_ARG, SPMM_ERR_CUDA, SPMM_ERR_OOM, SPMM_ERR_FORMAT, SPMM_ERR_TIMEOUT, SPMM_ERR_UNSUPPORTED = (
     -1, -2, -3, -4, -5, -6)
+SPMM_ERR_IO = -7
 SPMM_WANT_TRANSPOSE = 0x1
 SPMM_HOST_STREAMING = 0x2
 SPMM_REORDER = 0x4
+SPMM_FILE_DIRECT = 0x8
 
 _STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_FORMAT", -5: "ERR_TIMEOUT",
-           -6: "ERR_UNSUPPORTED"}
+           -6: "ERR_UNSUPPORTED", -7: "ERR_IO"}
 
 
 class SpmmError(RuntimeError):
@@ -110,6 +112,10 @@ _lib.spmm_apply_host.argtypes = [_P, _P, _i64, _i32, ctypes.c_int, _P, _i64, _i3
 _lib.spmm_apply_host.restype = ctypes.c_int
 _lib.spmm_apply_host_parts.argtypes = [_P, _P, _P, _P, _i32, ctypes.c_int, _i32, _P]
 _lib.spmm_apply_host_parts.restype = ctypes.c_int
+_lib.spmm_write_csr_file.argtypes = [ctypes.c_char_p, _i64, _i64, _i64, _P, _P, _P, ctypes.c_int]
+_lib.spmm_write_csr_file.restype = ctypes.c_int
+_lib.spmm_create_file.argtypes = [ctypes.POINTER(_P), ctypes.c_char_p, ctypes.c_uint32, _P, _P]
+_lib.spmm_create_file.restype = ctypes.c_int
 _lib.spmm_last_error.argtypes = []
 _lib.spmm_last_error.restype = ctypes.c_char_p
 
@@ -314,6 +320,29 @@ def spmm_create_tiles(n_rows, n_cols, tile, tiles, flags=0, opts: spmm_opts | No
     return h
 
 
+def spmm_write_csr_file(path, A, values=None) -> None:
+    """Write host CSR ``A`` (synth.CSR-like; values float32/bf16-as-uint16/float16
+    or None) to ``path`` in the library's file layout (host only)."""
+    rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
+    vals = A.values if values is None else values
+    vt, vp = SPMM_F32, None
+    if vals is not None:
+        vals = np.ascontiguousarray(vals)
+        vt = {np.dtype(np.float32): SPMM_F32, np.dtype(np.float16): SPMM_F16,
+              np.dtype(np.uint16): SPMM_BF16}[vals.dtype]
+        vp = _P(vals.ctypes.data)
+    _check(_lib.spmm_write_csr_file(os.fsencode(path), int(A.n_rows), int(A.n_cols), int(rp[-1]),
+                                    _P(rp.ctypes.data), _P(ci.ctypes.data), vp, vt))
+
+
+def spmm_create_file(path, direct=False, opts=None, stream=None):
+    h = _P(0)
+    _check(_lib.spmm_create_file(ctypes.byref(h), os.fsencode(path), SPMM_FILE_DIRECT if direct else 0,
+                                 ctypes.byref(opts) if opts is not None else None, _stream_handle(stream)))
+    return h
+
+
 def spmm_vpart_cols(n_in, n_out, p, xtype, budget_bytes) -> int:
     """Column-group width for vertical partitions under a device budget (host only)."""
     c = ctypes.c_int32(0)
@@ -435,6 +464,14 @@ class SparseMatrix:
         self.n_rows, self.n_cols = int(n_rows), int(n_cols)
         self.handle = spmm_create_tiles(n_rows, n_cols, tile, tiles, SPMM_WANT_TRANSPOSE if transpose else 0, opts,
                                         stream)
+        return self
+
+    @classmethod
+    def from_file(cls, path, n_rows, n_cols, direct=False, opts: spmm_opts | None = None, stream=None):
+        """Handle whose matrix stays in a file written by spmm_write_csr_file."""
+        self = cls.__new__(cls)
+        self.n_rows, self.n_cols = int(n_rows), int(n_cols)
+        self.handle = spmm_create_file(path, direct, opts, stream)
         return self
 
     @classmethod

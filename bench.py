@@ -703,10 +703,8 @@ def main():
     t_create = time.time() - t0
     # autotune the plan of each orientation on a short candidate list
     t0 = time.time()
-    cands = [dict(task_nnz=512, short_max=63, long_row=512, x_l2_policy=2),
-             dict(task_nnz=512, short_max=31, long_row=512, x_l2_policy=2),
-             dict(task_nnz=256, short_max=63, long_row=512, x_l2_policy=2),
-             dict(task_nnz=512, short_max=63, long_row=512, x_l2_policy=1)]
+    from paper_1602_02864_gb300.autotune import POWER_LAW_CANDIDATES
+    cands = POWER_LAW_CANDIDATES
     tuned = {}
     kt = 8 if 8 in ks else ks[0]
     best, times, _ = spmm.spmm_autotune(h.handle, kt, spmm.SPMM_F32, 0, cands, reps=2)

@@ -16,6 +16,13 @@ from . import spmm as _sp
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "spmm_autotune.json")
 
+# A short candidate list for power-law graphs: task size, the short-row limit
+# and the L2 policy of the X gathers are the knobs that mattered on R-MAT.
+POWER_LAW_CANDIDATES = [dict(task_nnz=512, short_max=63, long_row=512, x_l2_policy=2),
+                        dict(task_nnz=512, short_max=31, long_row=512, x_l2_policy=2),
+                        dict(task_nnz=256, short_max=63, long_row=512, x_l2_policy=2),
+                        dict(task_nnz=512, short_max=63, long_row=512, x_l2_policy=1)]
+
 
 def _key(h, k, xtype, transpose) -> str:
     import torch

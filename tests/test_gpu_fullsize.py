@@ -1,0 +1,153 @@
+"""Parity at the full sizes of the benchmark configurations.
+
+Sampled outputs are compared with the oracle, which computes them row by row,
+and properties that hold at any size are checked.  The launch configurations
+are the ones bench.py times: every plan its autotuner may choose, PageRank as
+one 30-iteration call, BF16 and FP32 X.  These tests hold up to ~15 GB on the
+device and several GB on the host, and take a few minutes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import assert_close_rel
+
+pytestmark = pytest.mark.gpu
+
+KS = [1, 2, 4, 8, 16, 32, 64]
+
+
+@pytest.fixture(scope="module")
+def sp():
+    from paper_1602_02864_gb300 import spmm
+    return spmm
+
+
+@pytest.fixture(scope="module")
+def rmat24():
+    """R-MAT scale 24 with 2^28 generated edges (the SpMM sweep and PageRank)."""
+    return synth.rmat_csr(24, seed=0)
+
+
+def test_rmat24_ksweep_every_candidate_plan(sp, rmat24):
+    import torch
+    from paper_1602_02864_gb300.autotune import POWER_LAW_CANDIDATES
+    A = rmat24
+    N = A.n_rows
+    h = sp.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, transpose=True)
+    Xh = synth.dense(N, 64, seed=0)
+    X = torch.from_numpy(Xh).cuda()
+    rows = np.unique(synth.sample_rows(N, 3000, seed=11))
+    rt = torch.from_numpy(rows).cuda()
+    th = oracle.num_threads()
+    ref = oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xh, rows, threads=th)
+    scale = oracle.spmm_rows(A.row_ptr, A.col_idx, None, np.abs(Xh), rows, threads=th)
+    ref_t = oracle.spmm_t_rows(N, N, A.row_ptr, A.col_idx, None, Xh[:, :1], rows)
+    scale_t = oracle.spmm_t_rows(N, N, A.row_ptr, A.col_idx, None, np.abs(Xh[:, :1]), rows)
+    Xi = synth.dense(N, 8, seed=5, mode="int")
+    ref_i = oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xi, rows, threads=th)
+    for c in POWER_LAW_CANDIDATES:
+        o = sp.spmm_opts(**c)
+        sp.spmm_replan(h.handle, o, 0)
+        for k in KS:
+            Y = h.apply(X[:, :k].contiguous())
+            assert_close_rel(Y[rt].cpu().numpy(), ref[:, :k], scale[:, :k], 1e-5, what=f"{c} k={k}")
+        Yi = h.apply(torch.from_numpy(Xi).cuda())
+        assert np.array_equal(Yi[rt].cpu().numpy().astype(np.float64), ref_i)      # integer mode: exact
+        sp.spmm_replan(h.handle, o, 1)
+        Yt = h.apply(X[:, :1].contiguous(), transpose=True)
+        assert_close_rel(Yt[rt].cpu().numpy(), ref_t, scale_t, 1e-5, what=f"{c} transpose")
+    h.sync_status()
+    h.close()
+
+
+def test_rmat24_bf16_x(sp, rmat24):
+    """BF16 X at k = 8 and 64: within 2e-3 of the oracle on the rounded inputs."""
+    import torch
+    A = rmat24
+    N = A.n_rows
+    h = sp.SparseMatrix(N, N, A.row_ptr, A.col_idx, None)
+    rows = np.unique(synth.sample_rows(N, 2000, seed=12))
+    rt = torch.from_numpy(rows).cuda()
+    for k in (8, 64):
+        Xb = torch.from_numpy(synth.dense(N, k, seed=k)).to(torch.bfloat16)
+        Xr = Xb.float().numpy()
+        ref = oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xr, rows, threads=oracle.num_threads())
+        scl = oracle.spmm_rows(A.row_ptr, A.col_idx, None, np.abs(Xr), rows, threads=oracle.num_threads())
+        Y = h.apply(Xb.cuda())
+        assert_close_rel(Y[rt].cpu().numpy(), ref, scl, 2e-3, what=f"bf16 k={k}")
+    h.close()
+
+
+def test_rmat24_pagerank_30_iterations(sp, rmat24):
+    A = rmat24
+    N = A.n_rows
+    h = sp.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, transpose=True)
+    x, res = h.pagerank(0.85, 30)
+    xg = x.double().cpu().numpy()
+    xr, resr = oracle.pagerank(N, A.row_ptr, A.col_idx, 0.85, 30)
+    assert np.all(np.abs(xg - xr) <= 1e-5 * xr + 1e-12), np.max(np.abs(xg - xr) / xr)
+    assert abs(xg.sum() - 1.0) < 1e-5 and xg.min() >= 0
+    np.testing.assert_allclose(res, resr, rtol=1e-3, atol=4 * 2.0 ** -24)
+    h.close()
+
+
+def test_sym_rmat25_lcc_spmm_and_eigensolver(sp):
+    """The eigensolver configuration at scale 25: the block product S V at
+    k = 16 (FP32 and BF16 X) on sampled rows, then a few restarts of the
+    solver, whose output must be orthonormal Ritz pairs of S in [-1, 1]."""
+    import torch
+    S = synth.sym_rmat_lcc(25, seed=0)
+    n = S.n_rows
+    h = sp.SparseMatrix.from_csr(S)
+    rows = np.unique(synth.sample_rows(n, 2000, seed=13))
+    rt = torch.from_numpy(rows).cuda()
+    Xh = synth.dense(n, 16, seed=2)
+    th = oracle.num_threads()
+    for dt, tol in ((torch.float32, 1e-5), (torch.bfloat16, 2e-3)):
+        Xd = torch.from_numpy(Xh).to(dt)
+        Xr = Xd.float().numpy()
+        ref = oracle.spmm_rows(S.row_ptr, S.col_idx, S.values, Xr, rows, threads=th)
+        scl = oracle.spmm_rows(S.row_ptr, S.col_idx, np.abs(S.values), np.abs(Xr), rows, threads=th)
+        Y = h.apply(Xd.cuda())
+        assert_close_rel(Y[rt].cpu().numpy(), ref, scl, tol, what=str(dt))
+    V0 = torch.from_numpy(synth.dense(n, 16, seed=1).astype(np.float64)).cuda()
+    V = torch.zeros((n, 8), dtype=torch.float64, device="cuda")
+    ev, rs, _ = h.eigs(8, V0, block=16, max_basis=64, max_restarts=3, tol=1e-5, evecs=V)
+    assert np.all(np.diff(ev) <= 0) and np.all(np.abs(ev) <= 1 + 1e-6) and np.all(rs >= 0)
+    G = (V.T @ V).cpu().numpy()
+    assert np.max(np.abs(G - np.eye(8))) < 1e-8
+    SV = h.apply(V.float()).double()                     # Rayleigh quotients through the FP32 product
+    rq = (V * SV).sum(dim=0).cpu().numpy()
+    np.testing.assert_allclose(rq, ev, atol=1e-5)
+    R = torch.linalg.norm(SV - V * torch.from_numpy(ev).cuda(), dim=0).cpu().numpy()
+    np.testing.assert_allclose(R, rs, rtol=0.05, atol=1e-5)
+    h.close()
+
+
+def test_chunglu256_batched_and_nmf(sp):
+    """256 Chung-Lu graphs in one block-diagonal handle: the batched product at
+    k = 16 on sampled rows of every graph, and 50 NMF steps (k = 16) whose
+    per-graph objectives never increase."""
+    import torch
+    graphs = [synth.chunglu_csr(g, seed=0) for g in range(256)]
+    h = sp.SparseMatrix.batched(graphs, transpose=True, weighted=False)
+    n = sum(g.n_rows for g in graphs)
+    Xh = synth.dense(n, 16, seed=3)
+    Y = h.apply(torch.from_numpy(Xh).cuda()).cpu().numpy()
+    r0 = 0
+    for gi, g in enumerate(graphs):
+        rows = np.unique(synth.sample_rows(g.n_rows, 16, seed=gi))
+        Xg = Xh[r0:r0 + g.n_cols]
+        ref = oracle.spmm_rows(g.row_ptr, g.col_idx, None, Xg, rows)
+        scl = oracle.spmm_rows(g.row_ptr, g.col_idx, None, np.abs(Xg), rows)
+        assert_close_rel(Y[r0 + rows], ref, scl, 1e-5, what=f"graph {gi}")
+        r0 += g.n_rows
+    W = torch.from_numpy(synth.dense(n, 16, seed=4, mode="unit")).cuda()
+    Ht = torch.from_numpy(synth.dense(n, 16, seed=5, mode="unit")).cuda()
+    obj = h.nmf(16, 50, W, Ht)
+    assert obj.shape == (256, 51)
+    assert np.all(obj[:, 1:] <= obj[:, :-1] * (1 + 1e-6) + 1e-9)
+    assert W.min().item() >= 0 and Ht.min().item() >= 0
+    h.close()

@@ -63,6 +63,11 @@ static void cut_blocks(const std::vector<int4>& tasks, int64_t n_rows, int64_t s
 static cudaError_t pin(const void* p, size_t bytes, bool* registered) {
     *registered = false;
     if (!p || bytes == 0) return cudaSuccess;
+    // memory that is page-locked already (cudaHostAlloc, or registered by the
+    // caller) is used as it is
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeHost) return cudaSuccess;
+    cudaGetLastError();
     cudaError_t e = cudaHostRegister(const_cast<void*>(p), bytes, cudaHostRegisterDefault);
     if (e == cudaErrorHostMemoryAlreadyRegistered) {
         cudaGetLastError();

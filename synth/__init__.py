@@ -43,6 +43,39 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+_CU_SRC = os.path.join(_HERE, "rmat_cuda.cu")
+_CU_LIB_PATH = os.path.join(_HERE, "libsynth_cuda.so")
+_cu_lib = None
+
+
+def build_cuda(force: bool = False) -> str:
+    """Compile libsynth_cuda.so (the GPU R-MAT generator) in place with nvcc."""
+    if force or not os.path.exists(_CU_LIB_PATH) or os.path.getmtime(_CU_LIB_PATH) < os.path.getmtime(_CU_SRC):
+        import shutil
+        nvcc = os.environ.get("NVCC") or shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+        tmp = _CU_LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-shared",
+                               "-Xcompiler", "-fPIC", "-o", tmp, _CU_SRC])
+        os.replace(tmp, _CU_LIB_PATH)
+    return _CU_LIB_PATH
+
+
+def _load_cuda():
+    global _cu_lib
+    with _lock:
+        if _cu_lib is None:
+            build_cuda()
+            lib = ctypes.CDLL(_CU_LIB_PATH)
+            P, i32, i64, u64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+            lib.synth_rmat_block_count.argtypes = [i32, i64, f64, f64, f64, u64, i32, P, P]
+            lib.synth_rmat_block_fill.argtypes = [i32, i64, f64, f64, f64, u64, i32, P, P, P, P, P]
+            lib.synth_host_alloc.argtypes = [u64]
+            lib.synth_host_alloc.restype = P
+            lib.synth_host_free.argtypes = [P]
+            _cu_lib = lib
+    return _cu_lib
+
+
 def _load():
     global _lib
     with _lock:
@@ -127,6 +160,90 @@ def uniform01(n: int, seed: int = 0, seed2: int = 0) -> np.ndarray:
     out = np.empty(n, dtype=np.float32)
     _load().synth_uniform01_f32(seed, seed2, n, _p(out))
     return out
+
+
+def host_empty(n: int, dtype) -> np.ndarray:
+    """An uninitialised host array in anonymous memory advised for transparent
+    huge pages (fewer, larger pages: pinned copies of it run at the full link
+    rate).  The mapping lives as long as the array."""
+    import mmap
+    dtype = np.dtype(dtype)
+    m = mmap.mmap(-1, max(int(n) * dtype.itemsize, 1), flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+    try:
+        m.madvise(mmap.MADV_HUGEPAGE)
+    except (AttributeError, OSError, ValueError):
+        pass
+    return np.frombuffer(m, dtype=dtype, count=int(n))
+
+
+def host_empty_pinned(n: int, dtype) -> np.ndarray:
+    """An uninitialised page-locked host array (cudaHostAlloc), freed when the
+    array and every view of it are gone."""
+    import weakref
+    lib = _load_cuda()
+    dtype = np.dtype(dtype)
+    nbytes = max(int(n) * dtype.itemsize, 1)
+    ptr = lib.synth_host_alloc(nbytes)
+    if not ptr:
+        raise MemoryError(f"cudaHostAlloc of {nbytes} bytes failed")
+    raw = (ctypes.c_uint8 * nbytes).from_address(ptr)
+    weakref.finalize(raw, lib.synth_host_free, ptr)
+    return np.frombuffer(raw, dtype=dtype, count=int(n))
+
+
+def rmat_csr_cuda(scale: int, n_edges: int | None = None, seed: int = 0, block_bits: int = 10,
+                  abc=RMAT_ABC, pinned: bool = False) -> CSR:
+    """rmat_csr (pattern) built on the GPU: the same draws, so the same graph,
+    for edge lists too large to sort on the host.  The edges are bucketed by
+    row block on the device (8 bytes per edge), each block is sorted and
+    deduplicated there, and the CSR is assembled in host memory (int64 row
+    pointers, int32 columns) -- page-locked memory if pinned (for streaming
+    the matrix to the GPU), else anonymous memory advised for huge pages."""
+    import torch
+    lib = _load_cuda()
+    n = 1 << scale
+    m = 16 * n if n_edges is None else int(n_edges)
+    a, b, c = abc
+    t0, t1, t2 = a, a + b, a + b + c
+    bb = min(block_bits, scale)
+    nb = 1 << bb
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    hist = torch.zeros(nb, dtype=torch.int64, device=dev)
+    if lib.synth_rmat_block_count(scale, m, t0, t1, t2, seed, bb, hist.data_ptr(), stream) != 0:
+        raise RuntimeError("synth_rmat_block_count failed")
+    base = torch.zeros(nb + 1, dtype=torch.int64, device=dev)
+    base[1:] = torch.cumsum(hist, 0)
+    keys = torch.empty(max(m, 1), dtype=torch.int64, device=dev)
+    cursor = torch.zeros(nb, dtype=torch.int64, device=dev)
+    overflow = torch.zeros(1, dtype=torch.int64, device=dev)
+    if lib.synth_rmat_block_fill(scale, m, t0, t1, t2, seed, bb, base.data_ptr(), cursor.data_ptr(),
+                                 keys.data_ptr(), overflow.data_ptr(), stream) != 0:
+        raise RuntimeError("synth_rmat_block_fill failed")
+    if int(overflow.item()) != 0 or not torch.equal(cursor, hist):
+        raise RuntimeError("R-MAT block fill does not match the block counts")
+    base_h = base.cpu().numpy()
+    rpb = n >> bb
+    alloc = host_empty_pinned if pinned else host_empty
+    row_ptr = alloc(n + 1, np.int64)
+    row_ptr[:] = 0
+    col = alloc(max(m, 1), np.int32)
+    col_t = torch.from_numpy(col)
+    nnz = 0
+    mask = n - 1
+    for blk in range(nb):
+        lo, hi = int(base_h[blk]), int(base_h[blk + 1])
+        if hi == lo:
+            continue
+        u = torch.unique_consecutive(torch.sort(keys[lo:hi])[0])
+        rows = (u >> scale) - blk * rpb
+        row_ptr[blk * rpb + 1:(blk + 1) * rpb + 1] = torch.bincount(rows, minlength=rpb).cpu().numpy()
+        col_t[nnz:nnz + u.numel()].copy_((u & mask).to(torch.int32))
+        nnz += u.numel()
+        del u, rows
+    del keys
+    np.cumsum(row_ptr, out=row_ptr)
+    return CSR(n, n, row_ptr, col[:nnz])
 
 
 def rmat_csr(scale: int, n_edges: int | None = None, seed: int = 0, weighted: bool = False,

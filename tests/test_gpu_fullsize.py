@@ -3,8 +3,9 @@
 Sampled outputs are compared with the oracle, which computes them row by row,
 and properties that hold at any size are checked.  The launch configurations
 are the ones bench.py times: every plan its autotuner may choose, PageRank as
-one 30-iteration call, BF16 and FP32 X.  These tests hold up to ~15 GB on the
-device and several GB on the host, and take a few minutes.
+one 30-iteration call, BF16 and FP32 X.  The scale-29 streaming test holds
+~190 GB of HBM while it generates its graph and ~85 GB of host memory; the
+others hold up to ~15 GB on the device.  Together they take a few minutes.
 """
 import numpy as np
 import pytest
@@ -150,4 +151,32 @@ def test_chunglu256_batched_and_nmf(sp):
     assert obj.shape == (256, 51)
     assert np.all(obj[:, 1:] <= obj[:, :-1] * (1 + 1e-6) + 1e-9)
     assert W.min().item() >= 0 and Ht.min().item() >= 0
+    h.close()
+
+
+def test_rmat29_streaming_sampled_rows(sp):
+    """The streaming configuration at full size: R-MAT scale 29 with average
+    degree 32 (~17 B nonzeros, ~73 GB of CSR in pinned host memory, built by
+    the GPU generator), X and Y of 2^29 x 4 FP32 in HBM; 10^5 sampled rows
+    against the oracle.  Needs ~100 GB of host memory and ~190 GB of HBM for
+    the generation."""
+    import os
+    import torch
+    host = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    dev_total = torch.cuda.mem_get_info()[1]
+    if host < 150e9 or dev_total < 200e9:
+        pytest.skip(f"needs ~150 GB host and ~200 GB device memory (have {host / 1e9:.0f}, {dev_total / 1e9:.0f})")
+    torch.cuda.empty_cache()
+    A = synth.rmat_csr_cuda(29, 32 << 29, seed=0, pinned=True)
+    torch.cuda.empty_cache()
+    N = A.n_rows
+    h = sp.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, streaming=True)
+    Xh = synth.dense(N, 4, seed=0)
+    Y = h.apply(torch.from_numpy(Xh).cuda())
+    rows = np.unique(synth.sample_rows(N, 100_000, seed=21))
+    th = oracle.num_threads()
+    ref = oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xh, rows, threads=th)
+    scl = oracle.spmm_rows(A.row_ptr, A.col_idx, None, np.abs(Xh), rows, threads=th)
+    assert_close_rel(Y[torch.from_numpy(rows).cuda()].cpu().numpy(), ref, scl, 1e-5)
+    h.sync_status()
     h.close()

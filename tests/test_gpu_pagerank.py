@@ -77,3 +77,28 @@ def test_pagerank_argument_errors(sp):
     with pytest.raises(sp.SpmmError):
         h.pagerank()
     h.close()
+
+
+@pytest.mark.parametrize("opts", [None, (32, 64, 64, 31), (512, 64, 512, 1)])
+def test_compensated_plan_gives_the_same_ranks(sp, opts):
+    """A compensated plan changes only how hub-row segments are summed, so its
+    ranks agree with the plain plan's within 1e-6 and with the oracle within
+    1e-5; plans with many split rows (small long_row) or one row per task are
+    included."""
+    A = synth.rmat_csr(14, seed=4)
+    o = None if opts is None else sp.spmm_opts(task_nnz=opts[0], task_rows=opts[1], long_row=opts[2],
+                                                 short_max=opts[3])
+    hf = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, transpose=True, opts=o)
+    oc = sp.spmm_opts(compensated=1) if o is None else sp.spmm_opts(task_nnz=opts[0], task_rows=opts[1],
+                                                                     long_row=opts[2], short_max=opts[3],
+                                                                     compensated=1)
+    hc = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, transpose=True, opts=oc)
+    xf, rf = hf.pagerank(0.85, 25)
+    xc, rc = hc.pagerank(0.85, 25)
+    xf, xc = xf.cpu().numpy().astype(np.float64), xc.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(xf - xc) <= 1e-6 * xc + 1e-12)
+    np.testing.assert_allclose(rf, rc, rtol=1e-3, atol=4 * 2.0 ** -24)
+    xr, _ = oracle.pagerank(A.n_rows, A.row_ptr, A.col_idx, 0.85, 25)
+    assert np.all(np.abs(xf - xr) <= 1e-5 * xr + 1e-12)
+    hf.close()
+    hc.close()

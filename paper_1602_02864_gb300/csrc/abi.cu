@@ -498,6 +498,10 @@ void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xty
             ya % (uintptr_t)(yv * 4) == 0)
             break;
     }
+    // A whole 16-byte X row on one lane (k = 4 FP32, k = 8 BF16/FP16) measured
+    // slower than two lanes of 8 bytes (BF16 k = 8: 2.27 -> 2.08 ms on R-MAT
+    // scale 24), so such rows get two lanes.
+    if (vec * esize == 16 && k == vec) vec >>= 1;
     const int nvec = k / vec;
     const int ch = nvec > 32 ? 2 : 1;
     const int per = (nvec + ch - 1) / ch;

@@ -749,6 +749,8 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     launches_per_apply = 1 + (1 if info["n_split_rows"] > 0 else 0)
+    # per PageRank call: init, scale, reduce, then per iteration the task
+    # kernel, the combine pass (if rows are split), the update and the reduce
     launches_per_pr_iter = 3 + (1 if info["n_split_rows_t"] > 0 else 0)
     xpr = torch.empty(N, dtype=torch.float32, device=dev)
     pr_res = [None]
@@ -992,7 +994,7 @@ def main():
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "gpu_launches": (launches_per_apply * len(ks) + launches_per_pr_iter * args.pagerank_iters
-                             + (4 if args.pagerank_iters else 0)) * args.steps,
+                             + (3 if args.pagerank_iters else 0)) * args.steps,
             "setup_s": {"generate": round(t_gen, 2), "create": round(t_create, 2), "autotune": round(t_tune, 2)},
             "autotuned_plan": tuned,
             "plan": {"tasks": info["n_tasks"], "split_rows": info["n_split_rows"], "segments": info["n_segments"]},

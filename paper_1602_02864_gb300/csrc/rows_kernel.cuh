@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "internal.h"
@@ -686,24 +687,27 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
 template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE>
 cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     using Lay = Layout<VMODE>;
-    static int blocks_per_sm = 0;   // per instantiation, computed once
-    static int num_sms = 0;
-    if (blocks_per_sm == 0) {
-        cudaError_t e;
-        if (Lay::kBlock > 48 * 1024) {
-            e = cudaFuncSetAttribute(rows_kernel<XT, VMODE, VEC, CH, COMP, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     Lay::kBlock);
-            if (e != cudaSuccess) return e;
-        }
+    // per instantiation, computed once (thread-safe; a failure is reported to
+    // every caller)
+    static std::once_flag once;
+    static int blocks_per_sm = 0, num_sms = 0;
+    static cudaError_t setup = cudaSuccess;
+    std::call_once(once, [] {
+        cudaError_t e = cudaSuccess;
+        if (Lay::kBlock > 48 * 1024)
+            e = cudaFuncSetAttribute(rows_kernel<XT, VMODE, VEC, CH, COMP, ONE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::kBlock);
         int dev = 0, nb = 0, sms = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rows_kernel<XT, VMODE, VEC, CH, COMP, ONE>,
-                                                               kWarpsPerBlock * 32, Lay::kBlock)) != cudaSuccess)
-            return e;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rows_kernel<XT, VMODE, VEC, CH, COMP, ONE>,
+                                                              kWarpsPerBlock * 32, Lay::kBlock);
+        setup = e;
         num_sms = sms;
         blocks_per_sm = nb > 0 ? nb : 1;
-    }
+    });
+    if (setup != cudaSuccess) return setup;
     const int64_t want = (a.n_tasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const int64_t cap = (int64_t)blocks_per_sm * num_sms;
     const dim3 grid((unsigned)(want < cap ? want : cap));

@@ -91,3 +91,36 @@ def test_plan_rejects_bad_row_ptr(sp):
     with pytest.raises(sp.SpmmError) as e:
         sp.spmm_plan_tasks(np.array([0, 3, 2], dtype=np.int64))
     assert e.value.status == sp.SPMM_ERR_FORMAT
+
+
+def test_plan_invariants_random_degrees(sp):
+    """Property test over random degree sequences and plan options: the plan
+    covers every row once, keeps every staging window in bounds, and splits a
+    hub row into segments of equal length except the last (the allocation-free
+    entry point finds a row's first segment from that)."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    degree = st.one_of(st.integers(0, 3), st.integers(0, 70), st.integers(0, 5000))
+
+    @hyp.settings(max_examples=150, deadline=None)
+    @hyp.given(deg=st.lists(degree, min_size=1, max_size=300),
+               task_nnz=st.integers(32, 512), task_rows=st.integers(1, 64),
+               long_row=st.integers(1, 512), short_max=st.integers(1, 511))
+    def prop(deg, task_nnz, task_rows, long_row, short_max):
+        n = len(deg)
+        rp = np.zeros(n + 1, dtype=np.int64)
+        rp[1:] = np.cumsum(deg)
+        A = synth.CSR(n, max(1, n), rp, np.zeros(int(rp[-1]), dtype=np.int32))
+        o = sp.spmm_opts(task_nnz=task_nnz, task_rows=task_rows, long_row=long_row, short_max=short_max)
+        tasks, n_split, n_seg = check_plan(sp, A, o)
+        e0 = (tasks[:, 2].astype(np.int64) & 0xFFFFFFFF) | (tasks[:, 3].astype(np.int64) << 32)
+        seg_rows = {}
+        for t in range(len(tasks) - 1):
+            if tasks[t, 1] < 0:
+                seg_rows.setdefault(int(tasks[t, 0]), []).append(int(e0[t + 1] - e0[t]))
+        assert len(seg_rows) == n_split
+        for lens in seg_rows.values():
+            assert len(lens) >= 2 and len(set(lens[:-1])) == 1 and lens[-1] <= lens[0]
+
+    prop()

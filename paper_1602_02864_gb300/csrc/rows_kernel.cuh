@@ -280,6 +280,9 @@ __device__ __forceinline__ void issue_task(const FwdArgs& a, const int4 d0, cons
 #ifndef SPMM_K1_FLAT
 #define SPMM_K1_FLAT 1            // k = 1 short-row runs: flat gather through shared memory
 #endif
+#ifndef SPMM_FLAT_UF
+#define SPMM_FLAT_UF 8            // k = 1 flat path: nonzeros gathered per lane per round
+#endif
 #ifndef SPMM_MERGE
 #define SPMM_MERGE 1              // one lane per X row: merge-based short-row runs
 #endif
@@ -383,7 +386,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
                 // products of rows j, j+32 in nonzero order from shared memory.
                 const int nr = d0.y;
                 int32_t* prod = const_cast<int32_t*>(st.col);
-                constexpr int UF = 8;
+                constexpr int UF = SPMM_FLAT_UF;
                 for (int base = 0; base < n; base += 32 * UF) {
                     float xv[UF], av[UF];
 #pragma unroll

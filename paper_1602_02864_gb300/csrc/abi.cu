@@ -9,10 +9,12 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -183,6 +185,24 @@ extern "C" const char* spmm_last_error(void) { return g_error.c_str(); }
 namespace spmm {
 
 // Host value of stored entry p (for ||A||^2 of each graph).
+// f(chunk, lo, hi) for `chunks` equal pieces of [0, n), on up to
+// hardware_concurrency host threads.
+template <class F>
+static void parallel_chunks(int64_t n, int chunks, F&& f) {
+    const int nt = std::max(1, std::min<int>(chunks, (int)std::thread::hardware_concurrency()));
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        for (int c; (c = next.fetch_add(1)) < chunks;) f(c, n * c / chunks, n * (c + 1) / chunks);
+    };
+    if (nt == 1 || n < (1 << 20)) {
+        worker();
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+    for (auto& t : pool) t.join();
+}
+
 static double host_value(const void* v, int32_t vtype, int64_t p) {
     if (!v) return 1.0;
     if (vtype == SPMM_F32) return (double)static_cast<const float*>(v)[p];
@@ -236,11 +256,33 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
             set_error(w + ": row_ptr decreases at row " + std::to_string(i));
             return SPMM_ERR_FORMAT;
         }
-    for (int64_t p = 0; p < nnz; ++p)
-        if (col_idx[p] < 0 || (int64_t)col_idx[p] >= n_cols) {
-            set_error(w + ": column index out of range at entry " + std::to_string(p));
+    // column range and ||A||_F^2 in 64 fixed chunks on host threads (the chunk
+    // sums are added in chunk order, so the norm does not depend on the thread
+    // count); the first bad entry is reported
+    constexpr int kChunks = 64;
+    std::vector<int64_t> bad(kChunks, -1);
+    std::vector<double> a2c(kChunks, 0.0);
+    parallel_chunks(nnz, kChunks, [&](int c, int64_t lo, int64_t hi) {
+        double acc = 0.0;
+        for (int64_t p = lo; p < hi; ++p) {
+            if (col_idx[p] < 0 || (int64_t)col_idx[p] >= n_cols) {
+                bad[c] = p;
+                return;
+            }
+            if (values) {
+                const double v = host_value(values, vtype, p);
+                acc += v * v;
+            }
+        }
+        a2c[c] = values ? acc : (double)(hi - lo);
+    });
+    for (int c = 0; c < kChunks; ++c)
+        if (bad[c] >= 0) {
+            set_error(w + ": column index out of range at entry " + std::to_string(bad[c]));
             return SPMM_ERR_FORMAT;
         }
+    double a2 = 0.0;
+    for (int c = 0; c < kChunks; ++c) a2 += a2c[c];
     const Params prm = resolve_params(opts);
 
     spmm_mat* A = new (std::nothrow) spmm_mat();
@@ -249,11 +291,6 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
     A->vtype = values ? (int32_t)vtype : -1;
     A->row_off = {0, n_rows};
     A->col_off = {0, n_cols};
-    double a2 = 0.0;
-    for (int64_t p = 0; p < nnz; ++p) {
-        const double v = host_value(values, vtype, p);
-        a2 += v * v;
-    }
     A->a2 = {a2};
     cudaError_t se = cudaMalloc((void**)&A->status, sizeof(int32_t));
     if (se == cudaSuccess) se = cudaMemsetAsync(A->status, 0, sizeof(int32_t), s);

@@ -4,8 +4,8 @@
  * The library computes Y = A X and Y = A^T X for a sparse n_rows x n_cols
  * matrix A (the adjacency matrix of a power-law graph, optionally weighted)
  * and a dense, row-major X with k = 1..64 columns: the operation of the
- * paper's Section 3 and Algorithm 1 ("SparseMatrixMultiply": every nonzero
- * a_ij of a sparse row adds a_ij * inM[j, :] to output row i; the dense
+ * paper's Section 3 and Algorithm 1 (every nonzero a_ij of a sparse row adds
+ * a_ij times row j of the input dense matrix to output row i; the dense
  * matrices are kept row-major, Section 3.3).
  *
  * Conventions for every entry point:
@@ -14,8 +14,9 @@
  *     available from spmm_last_error() (per calling thread) and any handle
  *     passed in is left unchanged.
  *   - Streams: work is enqueued on the given CUDA stream (cudaStream_t passed
- *     as void*, NULL = the legacy default stream).  spmm_apply does not
- *     synchronise the host and allocates nothing.
+ *     as void*, NULL = the legacy default stream).  spmm_apply on a resident
+ *     handle does not synchronise the host and allocates nothing (the two
+ *     exceptions are stated at spmm_apply).
  *   - Memory: X and Y are caller-owned DEVICE pointers; Y is overwritten, not
  *     accumulated into; X and Y must not overlap.  Handles own device copies of
  *     A made at create time.
@@ -222,9 +223,15 @@ int spmm_create_batched(spmm_mat_t* out, int32_t n_graphs, const int64_t* n_rows
  *          (A X) or n_cols (A^T X), leading dimension ldy >= k; only the first
  *          k columns of each row are written
  * Accumulation is float32 in a fixed order: repeated calls give bit-identical
- * results.  Asynchronous on `stream`; allocates nothing.
+ * results.  Asynchronous on `stream`; allocates nothing, except that a handle
+ * made with SPMM_REORDER grows its relabelled-X buffer the first time a
+ * larger n * k is used (which waits for the device), and a handle made by
+ * spmm_create_file blocks the calling thread until every block of the matrix
+ * has been read from its file.
  * Errors: SPMM_ERR_ARG (null, k out of range, ld < k, dtype, transpose without
- * SPMM_WANT_TRANSPOSE), SPMM_ERR_CUDA (launch failure).
+ * SPMM_WANT_TRANSPOSE), SPMM_ERR_UNSUPPORTED (16-bit values with another X
+ * type), SPMM_ERR_CUDA (launch failure); file handles also SPMM_ERR_IO and
+ * SPMM_ERR_FORMAT (see spmm_create_file).
  */
 int spmm_apply(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype xtype, void* Y,
                int64_t ldy, spmm_dtype ytype, int32_t transpose, void* stream);

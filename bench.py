@@ -42,7 +42,7 @@ L2_FLUSH_BYTES = 512 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=24)
@@ -802,16 +802,16 @@ def main():
     # ---- per-k breakdown; roofline of the dominant launch
     breakdown = {}
     for k in ks:
-        ms = statistics.mean(per_k[k])
+        ms = statistics.median(per_k[k])
         B = alg_bytes(nnz, N, N, k, 4)
         breakdown[str(k)] = {"ms": round(ms, 4), "nnz_per_s": nnz / (ms / 1e3), "alg_GBps": B / (ms / 1e3) / 1e9,
                              "roofline_frac": B / (ms / 1e3) / 1e9 / peak_gbs}
-    kdom = max(ks, key=lambda k: statistics.mean(per_k[k]))
+    kdom = max(ks, key=lambda k: statistics.median(per_k[k]))
     dom = breakdown[str(kdom)]
     dom_name = f"rows_kernel k={kdom} f32"
     pagerank = None
     if args.pagerank_iters:
-        ms = statistics.mean(pr_ms)
+        ms = statistics.median(pr_ms)
         it_ms = ms / args.pagerank_iters
         B = pagerank_iter_bytes(nnz, N)
         xh = xpr.double().cpu().numpy()
@@ -820,7 +820,7 @@ def main():
                     "roofline_frac": B / (it_ms / 1e3) / 1e9 / peak_gbs, "sum_x": float(xh.sum()),
                     "min_x": float(xh.min()), "residual_first_last": [float(pr_res[0][0]), float(pr_res[0][-1])]}
         pagerank["traffic"] = PAGERANK_ITER_TRAFFIC.get((args.scale, args.edge_factor))
-        if ms > statistics.mean(per_k[kdom]):
+        if ms > statistics.median(per_k[kdom]):
             dom = pagerank
             dom_name = ("PageRank iteration: rows_kernel on A^T (k=1, f32) + update + reduce; "
                         f"{args.pagerank_iters} per CUDA-graph launch, timed per call")

@@ -52,6 +52,7 @@ static void free_dev(DevCSR& d) {
     cudaFree(d.partials);
     cudaFree(d.partials_comp);
     cudaFree(d.perm);
+    cudaFree(d.task_ctr);
     d = DevCSR{};
 }
 
@@ -110,6 +111,11 @@ static int build_orientation(DevCSR& d, int64_t n_rows, int64_t n_cols, const in
     d.n_splits = (int64_t)plan.splits.size();
     d.n_segments = plan.n_segments;
     d.n_slots = plan.n_slots;
+    if ((e = cudaMalloc((void**)&d.task_ctr, sizeof(unsigned long long))) != cudaSuccess) {
+        d.task_ctr = nullptr;
+        return cuda_fail(e, "task counter");
+    }
+    *bytes += (int64_t)sizeof(unsigned long long);
     if (d.n_slots > 0) {
         size_t pb = (size_t)d.n_slots * kSlotStride * sizeof(float);
         if ((e = cudaMalloc((void**)&d.partials, pb)) != cudaSuccess) { d.partials = nullptr; return cuda_fail(e, "partials"); }
@@ -524,6 +530,13 @@ namespace spmm {
 
 // Lane geometry of one call: the widest vector that divides k and keeps every
 // X load and Y store aligned, lanes per nonzero and column chunks.
+unsigned long long* task_counter(const DevCSR& d, int32_t k, int32_t xtype, cudaStream_t s, cudaError_t* e) {
+    *e = cudaSuccess;
+    if (!d.task_ctr || (int64_t)k * (int64_t)dtype_size((spmm_dtype)xtype) < kDynamicRowBytes) return nullptr;
+    *e = cudaMemsetAsync(d.task_ctr, 0, sizeof(unsigned long long), s);
+    return *e == cudaSuccess ? d.task_ctr : nullptr;
+}
+
 void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xtype, const float* Y, int64_t ldy,
                   int* vec_out, int* ch_out) {
     const int esize = (int)dtype_size(xtype);
@@ -592,6 +605,9 @@ int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int3
     FwdArgs a;
     int vec = 1, ch = 1;
     set_geometry(a, X, ldx, k, xtype, Y, ldy, &vec, &ch);
+    cudaError_t ec = cudaSuccess;
+    a.task_ctr = task_counter(d, k, xtype, s, &ec);
+    if (ec != cudaSuccess) return cuda_fail(ec, "spmm_apply: task counter");
     a.row_ptr = d.row_ptr;
     a.col_idx = d.col_idx;
     a.val = d.val;

@@ -5,8 +5,9 @@
 // in the paper, 16-byte lane loads here), and each output row has a single
 // owner.
 //
-// Persistent warps walk the task list (plan.cpp) with a stride of the grid's
-// warp count.  Each warp stages a task's column indices, values and row
+// Persistent warps walk the task list (plan.cpp): with a stride of the grid's
+// warp count, or, for wide X rows, claiming their next task from an atomic
+// counter (FwdArgs::task_ctr).  Each warp stages a task's column indices, values and row
 // pointers into shared memory with bulk asynchronous copies (cp.async.bulk,
 // completion on an mbarrier) one task ahead, so the copy of task i+1 overlaps
 // the gathers of task i -- the GPU form of the paper's asynchronous tile-row
@@ -337,7 +338,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
     const uint64_t xpol = a.x_evict_last ? policy_evict_last() : policy_evict_normal();
     int4 d0 = a.tasks[t], d1 = a.tasks[t + 1];
     if (lane == 0) issue_task<VMODE>(a, d0, d1, wb, &bars[0], apol);
-    int64_t tn = t + W;
+    // the next task: static stride, or claimed from the counter by lane 0
+    auto next_task = [&](int64_t cur) -> int64_t {
+        if (!a.task_ctr) return cur + W;
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(a.task_ctr, 1ull);
+        return W + (int64_t)__shfl_sync(0xffffffffu, v, 0);
+    };
+    int64_t tn = next_task(t);
     int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
     if (tn < a.n_tasks) { n0 = a.tasks[tn]; n1 = a.tasks[tn + 1]; }
     uint32_t phase = 0;     // bit b = parity to wait for on buffer b
@@ -353,7 +361,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
             }
         }
         // prefetch the descriptor after next
-        const int64_t tnn = tn + W;
+        const int64_t tnn = tn < a.n_tasks ? next_task(tn) : a.n_tasks;
         int4 m0 = make_int4(0, 0, 0, 0), m1 = m0;
         if (tnn < a.n_tasks) { m0 = a.tasks[tnn]; m1 = a.tasks[tnn + 1]; }
 

@@ -132,6 +132,11 @@ int stream_setup(spmm_mat* A, const int64_t* row_ptr, const int32_t* col_idx, co
     d.n_splits = (int64_t)plan.splits.size();
     d.n_segments = plan.n_segments;
     d.n_slots = plan.n_slots;
+    if ((e = cudaMalloc((void**)&d.task_ctr, sizeof(unsigned long long))) != cudaSuccess) {
+        d.task_ctr = nullptr;
+        return cuda_fail(e, "streaming: task counter");
+    }
+    *bytes += (int64_t)sizeof(unsigned long long);
     if (d.n_slots > 0) {
         if ((e = cudaMalloc((void**)&d.partials, (size_t)d.n_slots * kSlotStride * sizeof(float))) != cudaSuccess)
             return cuda_fail(e, "streaming: partials");
@@ -240,6 +245,8 @@ int stream_apply(const spmm_mat* A, const void* X, int64_t ldx, int32_t k, int32
         a.row_ptr = S.slot_rp[slot] - b.r0;
         a.tasks = d.tasks + b.t0;
         a.n_tasks = b.t1 - b.t0;
+        a.task_ctr = task_counter(d, k, xtype, s, &e);
+        if (e != cudaSuccess) break;
         if ((e = launch_rows(a, xtype, vmode, vec, ch, s)) != cudaSuccess) break;
         if ((e = cudaEventRecord(S.freed[slot], s)) != cudaSuccess) break;
     }

@@ -530,9 +530,11 @@ namespace spmm {
 
 // Lane geometry of one call: the widest vector that divides k and keeps every
 // X load and Y store aligned, lanes per nonzero and column chunks.
-unsigned long long* task_counter(const DevCSR& d, int32_t k, int32_t xtype, cudaStream_t s, cudaError_t* e) {
+unsigned long long* task_counter(const DevCSR& d, int32_t k, int32_t xtype, cudaStream_t s, cudaError_t* e,
+                                 int32_t* chunk) {
     *e = cudaSuccess;
-    if (!d.task_ctr || (int64_t)k * (int64_t)dtype_size((spmm_dtype)xtype) < kDynamicRowBytes) return nullptr;
+    *chunk = (int64_t)k * (int64_t)dtype_size((spmm_dtype)xtype) >= kWideRowBytes ? 1 : kNarrowTaskChunk;
+    if (!d.task_ctr) return nullptr;
     *e = cudaMemsetAsync(d.task_ctr, 0, sizeof(unsigned long long), s);
     return *e == cudaSuccess ? d.task_ctr : nullptr;
 }
@@ -606,7 +608,7 @@ int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int3
     int vec = 1, ch = 1;
     set_geometry(a, X, ldx, k, xtype, Y, ldy, &vec, &ch);
     cudaError_t ec = cudaSuccess;
-    a.task_ctr = task_counter(d, k, xtype, s, &ec);
+    a.task_ctr = task_counter(d, k, xtype, s, &ec, &a.task_chunk);
     if (ec != cudaSuccess) return cuda_fail(ec, "spmm_apply: task counter");
     a.row_ptr = d.row_ptr;
     a.col_idx = d.col_idx;

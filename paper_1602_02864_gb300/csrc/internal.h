@@ -170,9 +170,10 @@ void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
               int64_t ldy, cudaStream_t s);
-// the task counter for a launch over rows of k elements of xtype (reset on s),
-// or nullptr for the static schedule
-unsigned long long* task_counter(const DevCSR& d, int32_t k, int32_t xtype, cudaStream_t s, cudaError_t* e);
+// the task counter for a launch over rows of k elements of xtype (reset on s;
+// nullptr for the static schedule) and the number of tasks per claim
+unsigned long long* task_counter(const DevCSR& d, int32_t k, int32_t xtype, cudaStream_t s, cudaError_t* e,
+                                 int32_t* chunk);
 struct FwdArgs;
 void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xtype, const float* Y, int64_t ldy,
                   int* vec_out, int* ch_out);
@@ -208,17 +209,22 @@ struct FwdArgs {
     int32_t compensated;  // long rows / hub segments: compensated summation
     float* partials_comp; // compensation term of each segment partial (compensated only)
     // Dynamic scheduling: after its first task (static, one per warp), a warp
-    // claims task W + atomicAdd(task_ctr, 1) (W = warps in the grid); the
-    // counter is zero at launch.  nullptr: tasks t, t + W, t + 2W, ...
+    // claims the next task_chunk tasks, from W + task_chunk * atomicAdd(task_ctr,
+    // 1) on (W = warps in the grid); the counter is zero at launch.  nullptr:
+    // tasks t, t + W, t + 2W, ...
     unsigned long long* task_ctr = nullptr;
+    int32_t task_chunk = 1;
 };
 
-// Wide X rows (at least this many bytes) are scheduled dynamically: their
-// tasks vary more in time (gathers that miss L2), and balancing them paid
-// (R-MAT scale 24, FP32: k = 4 1.95 -> 1.92 ms, k = 16 3.97 -> 3.22 ms), while
-// for narrow rows the counter's atomics cost more than they save (k = 1
-// 1.11 -> 1.38 ms, k = 2 1.46 -> 1.53 ms).
-constexpr int kDynamicRowBytes = 16;
+// Launches from a handle are scheduled dynamically.  Tasks over wide X rows
+// (at least kWideRowBytes bytes) vary a lot in time (gathers that miss L2)
+// and are claimed one at a time (R-MAT scale 24, FP32: k = 4 1.95 -> 1.92 ms,
+// k = 16 3.97 -> 3.22 ms against the static stride).  Narrow-row tasks are
+// short, and claiming them one at a time made the counter's atomics the
+// bottleneck (k = 1 1.11 -> 1.38 ms), so they are claimed kNarrowTaskChunk at
+// a time (k = 1 on A^T 1.15 -> 1.11 ms, 30 PageRank iterations 40.5 -> 38.0 ms).
+constexpr int kWideRowBytes = 16;
+constexpr int kNarrowTaskChunk = 4;
 
 // rows_*.cu: launch the task kernel for one X dtype.  vmode: 0 pattern,
 // 1 f32 values, 2 bf16 values, 3 f16 values.  Returns a cudaError_t.

@@ -5,9 +5,10 @@
 // in the paper, 16-byte lane loads here), and each output row has a single
 // owner.
 //
-// Persistent warps walk the task list (plan.cpp): with a stride of the grid's
-// warp count, or, for wide X rows, claiming their next task from an atomic
-// counter (FwdArgs::task_ctr).  Each warp stages a task's column indices, values and row
+// Persistent warps walk the task list (plan.cpp), claiming their next tasks
+// from an atomic counter (one task at a time for wide X rows, a few for narrow
+// ones; FwdArgs::task_ctr), or, without a counter, with a stride of the grid's
+// warp count.  Each warp stages a task's column indices, values and row
 // pointers into shared memory with bulk asynchronous copies (cp.async.bulk,
 // completion on an mbarrier) one task ahead, so the copy of task i+1 overlaps
 // the gathers of task i -- the GPU form of the paper's asynchronous tile-row
@@ -338,12 +339,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
     const uint64_t xpol = a.x_evict_last ? policy_evict_last() : policy_evict_normal();
     int4 d0 = a.tasks[t], d1 = a.tasks[t + 1];
     if (lane == 0) issue_task<VMODE>(a, d0, d1, wb, &bars[0], apol);
-    // the next task: static stride, or claimed from the counter by lane 0
+    // the next task: static stride, or the next of a chunk claimed from the
+    // counter by lane 0
+    int64_t cnext = 0, cend = 0;
     auto next_task = [&](int64_t cur) -> int64_t {
         if (!a.task_ctr) return cur + W;
+        if (cnext < cend) return cnext++;
         unsigned long long v = 0;
         if (lane == 0) v = atomicAdd(a.task_ctr, 1ull);
-        return W + (int64_t)__shfl_sync(0xffffffffu, v, 0);
+        cnext = W + (int64_t)__shfl_sync(0xffffffffu, v, 0) * a.task_chunk;
+        cend = cnext + a.task_chunk;
+        return cnext++;
     };
     int64_t tn = next_task(t);
     int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;

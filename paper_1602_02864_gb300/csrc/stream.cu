@@ -245,7 +245,7 @@ int stream_apply(const spmm_mat* A, const void* X, int64_t ldx, int32_t k, int32
         a.row_ptr = S.slot_rp[slot] - b.r0;
         a.tasks = d.tasks + b.t0;
         a.n_tasks = b.t1 - b.t0;
-        a.task_ctr = task_counter(d, k, xtype, s, &e);
+        a.task_ctr = task_counter(d, k, xtype, s, &e, &a.task_chunk);
         if (e != cudaSuccess) break;
         if ((e = launch_rows(a, xtype, vmode, vec, ch, s)) != cudaSuccess) break;
         if ((e = cudaEventRecord(S.freed[slot], s)) != cudaSuccess) break;

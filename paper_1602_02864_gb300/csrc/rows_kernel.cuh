@@ -19,7 +19,9 @@
 // A warp is cut into G = 32 / LANES lane groups; LANES lanes cover one X row
 // (each lane VEC consecutive elements, CH chunks of them).
 //   short-row task: group g owns rows g, g+G, ... of the run and sums each
-//                   row's nonzeros in order;
+//                   row's nonzeros in order (with one lane per X row, k = 1
+//                   takes the flat path and rows of up to 8 bytes the
+//                   merge-based path, both described at their branches);
 //   long row / hub segment: group g takes nonzeros g, g+G, g+2G, ...; the
 //                   groups' partial sums are added by a fixed xor-shuffle
 //                   tree; a segment writes its sum to a partial slot.

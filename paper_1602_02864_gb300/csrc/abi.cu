@@ -566,6 +566,12 @@ void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xty
     a.k = k;
     a.lanes_log2 = lg;
     a.nvec = nvec;
+    // merge-based short-row runs over lane groups measured faster for rows
+    // on 4 or more lanes and for lanes of at most 8 bytes (R-MAT scale 24,
+    // FP32: k = 4 1.87 -> 1.79 ms, k = 16 3.27 -> 2.98, k = 32 4.52 -> 4.18),
+    // slower for 32-byte rows on two lanes (k = 8 2.21 -> 2.33); lanes of 8
+    // 16-bit elements spill in that path and keep the row walk
+    a.merge_groups = ch == 1 && lg >= 1 && vec <= 4 && (lg >= 2 || vec * esize <= 8);
     *vec_out = vec;
     *ch_out = ch;
 }

@@ -214,6 +214,9 @@ struct FwdArgs {
     // tasks t, t + W, t + 2W, ...
     unsigned long long* task_ctr = nullptr;
     int32_t task_chunk = 1;
+    // short-row runs over rows of several lanes: 1 = merge-based pieces per
+    // lane group, 0 = each group walks whole rows
+    int32_t merge_groups = 0;
 };
 
 // Launches from a handle are scheduled dynamically.  Tasks over wide X rows
@@ -235,6 +238,10 @@ cudaError_t launch_rows_f16(const FwdArgs& a, int vmode, int vec, int ch, cudaSt
 cudaError_t launch_rows_f32_one(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
 cudaError_t launch_rows_bf16_one(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
 cudaError_t launch_rows_f16_one(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
+// merge-based short-row runs over lane groups (ch == 1, FwdArgs::merge_groups)
+cudaError_t launch_rows_f32_mg(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
+cudaError_t launch_rows_bf16_mg(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
+cudaError_t launch_rows_f16_mg(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
 
 // combine.cu: Y[row] = sum of the split row's partials in segment order.
 cudaError_t launch_combine(const int4* splits, int64_t n_splits, const float* partials, float* Y,

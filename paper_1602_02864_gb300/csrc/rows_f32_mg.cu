@@ -1,0 +1,12 @@
+// rows_f32_mg.cu -- row-task kernel instantiations for float X whose short-row
+// runs are split into equal pieces per lane group (merge-based), in their own
+// translation unit so they compile in parallel with the others.
+#include "rows_kernel.cuh"
+
+namespace spmm {
+
+cudaError_t launch_rows_f32_mg(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
+    return launch_rows_t<float, false, true>(a, vmode, vec, ch, s);
+}
+
+}  // namespace spmm

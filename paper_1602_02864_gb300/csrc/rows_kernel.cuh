@@ -21,7 +21,9 @@
 //   short-row task: group g owns rows g, g+G, ... of the run and sums each
 //                   row's nonzeros in order (with one lane per X row, k = 1
 //                   takes the flat path and rows of up to 8 bytes the
-//                   merge-based path, both described at their branches);
+//                   merge-based path; the MG instantiations cut the run
+//                   into equal pieces per lane group instead: all three
+//                   are described at their branches);
 //   long row / hub segment: group g takes nonzeros g, g+G, g+2G, ...; the
 //                   groups' partial sums are added by a fixed xor-shuffle
 //                   tree; a segment writes its sum to a partial slot.
@@ -290,20 +292,25 @@ __device__ __forceinline__ void issue_task(const FwdArgs& a, const int4 d0, cons
 #ifndef SPMM_MERGE
 #define SPMM_MERGE 1              // one lane per X row: merge-based short-row runs
 #endif
+
 #ifndef SPMM_MIN_BLOCKS
 #define SPMM_MIN_BLOCKS 4         // resident blocks per SM the register budget targets
 #endif
 
 // ONE: one lane per X row (k == VEC, CH == 1); the lane geometry is then a
 // compile-time constant and short-row runs take the flat (k = 1) or, for X
-// rows of up to 8 bytes, the merge-based path.
-template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE>
+// rows of up to 8 bytes, the merge-based path.  MG: several lanes per X row
+// (CH == 1) and short-row runs merge-based over lane groups.
+template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, bool MG = false>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOCKS) rows_kernel(FwdArgs a) {
     static_assert(!ONE || CH == 1, "one lane per row needs CH == 1");
+    static_assert(!MG || (!ONE && CH == 1), "merge over lane groups needs several lanes and CH == 1");
     constexpr bool kFlat = ONE && VEC == 1 && SPMM_K1_FLAT;
     // merge-based runs pay off for X rows of up to 8 bytes; for 16-byte rows
     // (mostly gathered from DRAM) the row-per-lane walk measured faster
     constexpr bool kMerge = ONE && !kFlat && SPMM_MERGE && VEC * sizeof(XT) <= 8;
+    // the same over lane groups, for rows that need several lanes (MG)
+    constexpr bool kMergeG = MG;
     using Lay = Layout<VMODE>;
     // nonzeros in flight per lane group
     constexpr int kBytes = VEC * CH * (int)sizeof(XT);
@@ -313,6 +320,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
 #define SPMM_MERGE_UNROLL 2
 #endif
     constexpr int UM = U < SPMM_MERGE_UNROLL ? U : SPMM_MERGE_UNROLL;   // merge path: nonzeros in flight per lane
+#ifndef SPMM_MERGE_WIDE_UNROLL
+#define SPMM_MERGE_WIDE_UNROLL 2
+#endif
+    constexpr int UW = U < SPMM_MERGE_WIDE_UNROLL ? U : SPMM_MERGE_WIDE_UNROLL;   // per lane group
     extern __shared__ __align__(128) unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* wb = smem + w * Lay::kWarp;
@@ -541,7 +552,101 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
                     head[v] = prev + head[v];
                 }
                 if (hrow >= 0) store_y<VEC>(a.Y + (int64_t)(d0.x + hrow) * a.ldy, head);
-            } else if (!kFlat && !kMerge && d0.y > 0) {
+            } else if (kMergeG && d0.y > 0) {
+                // run of short rows, LANES lanes per X row (merge-based over lane
+                // groups): the task's nonzeros are cut into G equal contiguous
+                // pieces, group g taking piece g, so every group gathers about
+                // n/G rows of X whatever the row lengths.  As in the one-lane
+                // case, a row crossing pieces is finished by a segmented scan
+                // over the groups' tails (shfl_up by multiples of LANES, so lane
+                // li of a group meets lane li of the others) and its head.
+                const int nr = d0.y;
+                for (int j = g; j < nr; j += G)           // rows without nonzeros
+                    if (st.rp[j] == st.rp[j + 1] && act[0]) {
+                        float z[VEC];
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) z[v] = 0.f;
+                        store_y<VEC>(a.Y + (int64_t)(d0.x + j) * a.ldy + li * VEC, z);
+                    }
+                const int per = (n + G - 1) / G;
+                const int cs = min(n, g * per), ce = min(n, cs + per);
+                float tail[VEC], head[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) tail[v] = 0.f, head[v] = 0.f;
+                int key = -1 - g;                         // tail row, or a key no other group has
+                int hrow = -1;                            // head row
+                if (cs < ce) {
+                    int lo = 0, hi = nr - 1;              // the row holding nonzero cs
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if ((int)(st.rp[mid] - e0) <= cs) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    int r = lo;
+                    int rs = (int)(st.rp[r] - e0), re = (int)(st.rp[r + 1] - e0);
+                    float acc[VEC];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+                    for (int i = cs; i < ce; i += UW) {
+                        XVec<XT, VEC> xv[UW];
+                        float av[UW];
+#pragma unroll
+                        for (int u = 0; u < UW; ++u)
+                            if (i + u < ce) {
+                                const int64_t cidx = st.col[i + u];
+                                av[u] = staged_val<VMODE>(st.val, i + u);
+                                if (act[0]) xv[u].load(xb + cidx * a.ldx, xpol);
+                            }
+#pragma unroll
+                        for (int u = 0; u < UW; ++u)
+                            if (i + u < ce) {
+                                while (i + u >= re) {             // row r ended inside the piece
+                                    if (rs < re) {
+                                        if (rs >= cs) {
+                                            if (act[0]) store_y<VEC>(a.Y + (int64_t)(d0.x + r) * a.ldy + li * VEC, acc);
+                                        } else {
+                                            hrow = r;
+#pragma unroll
+                                            for (int v = 0; v < VEC; ++v) head[v] = acc[v];
+                                        }
+                                    }
+#pragma unroll
+                                    for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+                                    ++r;
+                                    rs = re;
+                                    re = (int)(st.rp[r + 1] - e0);
+                                }
+                                if (act[0]) {
+#pragma unroll
+                                    for (int v = 0; v < VEC; ++v) acc[v] = fmaf(av[u], xv[u].get(v), acc[v]);
+                                }
+                            }
+                    }
+                    if (re > ce) {                        // the row holding nonzero ce - 1
+                        key = r;
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) tail[v] = acc[v];
+                    } else if (rs >= cs) {
+                        if (act[0]) store_y<VEC>(a.Y + (int64_t)(d0.x + r) * a.ldy + li * VEC, acc);
+                    } else {
+                        hrow = r;
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) head[v] = acc[v];
+                    }
+                }
+                for (int off = 1; off < G; off <<= 1) {
+                    const int kup = __shfl_up_sync(0xffffffffu, key, off * LANES);
+                    float up[VEC];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) up[v] = __shfl_up_sync(0xffffffffu, tail[v], off * LANES);
+                    if (g >= off && kup == key)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) tail[v] += up[v];
+                }
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) head[v] += __shfl_up_sync(0xffffffffu, tail[v], LANES);
+                if (hrow >= 0 && act[0]) store_y<VEC>(a.Y + (int64_t)(d0.x + hrow) * a.ldy + li * VEC, head);
+            } else if (!kFlat && !kMerge && !kMergeG && d0.y > 0) {
                 // run of short rows: lane group g owns rows g, g+G, ...
                 const int nr = d0.y;
                 for (int j = g; j < nr; j += G) {
@@ -703,7 +808,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
     }
 }
 
-template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE>
+template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, bool MG = false>
 cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     using Lay = Layout<VMODE>;
     // per instantiation, computed once (thread-safe; a failure is reported to
@@ -714,13 +819,13 @@ cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     std::call_once(once, [] {
         cudaError_t e = cudaSuccess;
         if (Lay::kBlock > 48 * 1024)
-            e = cudaFuncSetAttribute(rows_kernel<XT, VMODE, VEC, CH, COMP, ONE>,
+            e = cudaFuncSetAttribute(rows_kernel<XT, VMODE, VEC, CH, COMP, ONE, MG>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::kBlock);
         int dev = 0, nb = 0, sms = 0;
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rows_kernel<XT, VMODE, VEC, CH, COMP, ONE>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rows_kernel<XT, VMODE, VEC, CH, COMP, ONE, MG>,
                                                               kWarpsPerBlock * 32, Lay::kBlock);
         setup = e;
         num_sms = sms;
@@ -730,18 +835,29 @@ cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     const int64_t want = (a.n_tasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const int64_t cap = (int64_t)blocks_per_sm * num_sms;
     const dim3 grid((unsigned)(want < cap ? want : cap));
-    rows_kernel<XT, VMODE, VEC, CH, COMP, ONE><<<grid, kWarpsPerBlock * 32, Lay::kBlock, s>>>(a);
+    rows_kernel<XT, VMODE, VEC, CH, COMP, ONE, MG><<<grid, kWarpsPerBlock * 32, Lay::kBlock, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename XT, bool ONE>
+template <typename XT, bool ONE, bool MG = false>
 cudaError_t launch_rows_t(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
+    static_assert(!(ONE && MG), "one lane per row has no lane groups");
     if (a.n_tasks <= 0) return cudaSuccess;
 #define SPMM_LAUNCH(VM, V, C)                                                            \
     if (vmode == VM && vec == V && ch == C)                                              \
-        return a.compensated ? launch_one<XT, VM, V, C, true, ONE>(a, s)                 \
-                             : launch_one<XT, VM, V, C, false, ONE>(a, s);
-    if constexpr (ONE) {
+        return a.compensated ? launch_one<XT, VM, V, C, true, ONE, MG>(a, s)             \
+                             : launch_one<XT, VM, V, C, false, ONE, MG>(a, s);
+    if constexpr (MG) {          // CH == 1, at most 4 elements per lane
+        if constexpr (sizeof(XT) == 4) {
+            SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1)
+            SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1)
+        } else {
+            constexpr int VM3 = std::is_same<XT, __half>::value ? 3 : 2;
+            SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1)
+            SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1)
+            SPMM_LAUNCH(VM3, 4, 1) SPMM_LAUNCH(VM3, 2, 1) SPMM_LAUNCH(VM3, 1, 1)
+        }
+    } else if constexpr (ONE) {  // CH == 1 only
         if constexpr (sizeof(XT) == 4) {
             SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1)
             SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1)

@@ -134,7 +134,9 @@ def test_plan_shapes_agree(sp, opts):
 @pytest.mark.parametrize("task_nnz", [32, 100, 512])
 def test_merge_rows_cross_lane_pieces(sp, kind, task_nnz):
     """One lane per X row (k = 2 in FP32, k = 2 and 4 in BF16) cuts each
-    short-row run into 32 equal pieces of nonzeros; rows that start before a
+    short-row run into 32 equal pieces of nonzeros, and rows on several lanes
+    of at most 4 elements (k = 4, 16, 32, 64 in FP32; 8, 16, 32 in BF16 and
+    FP16) cut it into one piece per lane group; rows that start before a
     piece, span several pieces or have no nonzeros must all come out right.
     Degree mixes: uniform 0..63, geometric, mostly 0..2 with 10% of 30..63,
     and 0/1."""
@@ -161,11 +163,22 @@ def test_merge_rows_cross_lane_pieces(sp, kind, task_nnz):
             Yb = hp.apply(Xb, transpose=tr).cpu().numpy().astype(np.float64)
             ref = oracle.spmm(n, n, A.row_ptr, A.col_idx, None, Xb.float().cpu().numpy(), transpose=tr)
             assert np.array_equal(Yb, ref)
-        Xf = synth.dense(n, 2, seed=7)
-        Yw = hw.apply(to_dev(Xf), transpose=tr).cpu().numpy()
-        ref = oracle.spmm(n, n, A.row_ptr, A.col_idx, A.values, Xf, transpose=tr)
-        scale = oracle.spmm(n, n, A.row_ptr, A.col_idx, A.values, np.abs(Xf), transpose=tr)
-        assert_close_rel(Yw, ref, scale, 1e-5)
+        for k in (4, 16, 32, 64):
+            X = synth.dense(n, k, seed=8 + k, mode="int")
+            Y = hp.apply(to_dev(X), transpose=tr).cpu().numpy().astype(np.float64)
+            assert np.array_equal(Y, oracle.spmm(n, n, A.row_ptr, A.col_idx, None, X, transpose=tr)), k
+        for dt in (torch.bfloat16, torch.float16):
+            for k in (8, 16, 32):
+                Xb = torch.from_numpy(synth.dense(n, k, seed=k, mode="int")).to(dt).cuda()
+                Yb = hp.apply(Xb, transpose=tr).cpu().numpy().astype(np.float64)
+                ref = oracle.spmm(n, n, A.row_ptr, A.col_idx, None, Xb.float().cpu().numpy(), transpose=tr)
+                assert np.array_equal(Yb, ref), (dt, k)
+        for k in (2, 16):
+            Xf = synth.dense(n, k, seed=7)
+            Yw = hw.apply(to_dev(Xf), transpose=tr).cpu().numpy()
+            ref = oracle.spmm(n, n, A.row_ptr, A.col_idx, A.values, Xf, transpose=tr)
+            scale = oracle.spmm(n, n, A.row_ptr, A.col_idx, A.values, np.abs(Xf), transpose=tr)
+            assert_close_rel(Yw, ref, scale, 1e-5)
     hp.sync_status()
     hp.close()
     hw.close()

@@ -6,7 +6,7 @@
 namespace spmm {
 
 cudaError_t launch_rows_f16_mg(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
-    return launch_rows_t<__half, false, true>(a, vmode, vec, ch, s);
+    return launch_rows_t<__half, false, 1>(a, vmode, vec, ch, s);
 }
 
 }  // namespace spmm

@@ -294,23 +294,36 @@ __device__ __forceinline__ void issue_task(const FwdArgs& a, const int4 d0, cons
 #endif
 
 #ifndef SPMM_MIN_BLOCKS
-#define SPMM_MIN_BLOCKS 4         // resident blocks per SM the register budget targets
+#define SPMM_MIN_BLOCKS 3         // resident blocks per SM the register budget targets (80 registers)
 #endif
+
+// Resident blocks per SM that the register budget of an instantiation targets.
+// Three blocks (80 registers a thread) measured faster than four (64) for
+// every path but the pattern group merge over rows on 8 or more lanes
+// (R-MAT scale 24, FP32: k = 1 1.10 -> 0.93 ms, k = 8 2.23 -> 1.92, 30
+// PageRank iterations 35.9 -> 31.6 ms; k = 32 4.20 -> 4.34, k = 64
+// 7.59 -> 7.91), which keeps four in its own variant (MG == 2).
+template <int VMODE, int MG>
+constexpr int min_blocks() {
+    return (MG == 2 && VMODE == 0) ? 4 : SPMM_MIN_BLOCKS;
+}
 
 // ONE: one lane per X row (k == VEC, CH == 1); the lane geometry is then a
 // compile-time constant and short-row runs take the flat (k = 1) or, for X
-// rows of up to 8 bytes, the merge-based path.  MG: several lanes per X row
-// (CH == 1) and short-row runs merge-based over lane groups.
-template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, bool MG = false>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOCKS) rows_kernel(FwdArgs a) {
+// rows of up to 8 bytes, the merge-based path.  MG != 0: several lanes per X
+// row (CH == 1) and short-row runs merge-based over lane groups, with 3
+// blocks per SM and 4 nonzeros in flight per group (MG == 1) or 4 blocks and
+// 2 in flight (MG == 2).
+template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, int MG = 0>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())) rows_kernel(FwdArgs a) {
     static_assert(!ONE || CH == 1, "one lane per row needs CH == 1");
-    static_assert(!MG || (!ONE && CH == 1), "merge over lane groups needs several lanes and CH == 1");
+    static_assert(MG == 0 || (!ONE && CH == 1), "merge over lane groups needs several lanes and CH == 1");
     constexpr bool kFlat = ONE && VEC == 1 && SPMM_K1_FLAT;
     // merge-based runs pay off for X rows of up to 8 bytes; for 16-byte rows
     // (mostly gathered from DRAM) the row-per-lane walk measured faster
     constexpr bool kMerge = ONE && !kFlat && SPMM_MERGE && VEC * sizeof(XT) <= 8;
     // the same over lane groups, for rows that need several lanes (MG)
-    constexpr bool kMergeG = MG;
+    constexpr bool kMergeG = MG != 0;
     using Lay = Layout<VMODE>;
     // nonzeros in flight per lane group
     constexpr int kBytes = VEC * CH * (int)sizeof(XT);
@@ -321,9 +334,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
 #endif
     constexpr int UM = U < SPMM_MERGE_UNROLL ? U : SPMM_MERGE_UNROLL;   // merge path: nonzeros in flight per lane
 #ifndef SPMM_MERGE_WIDE_UNROLL
-#define SPMM_MERGE_WIDE_UNROLL 2
+#define SPMM_MERGE_WIDE_UNROLL 4
 #endif
-    constexpr int UW = U < SPMM_MERGE_WIDE_UNROLL ? U : SPMM_MERGE_WIDE_UNROLL;   // per lane group
+    // merge over lane groups: nonzeros in flight per group (4 spill at 64
+    // registers, and with staged values at 80)
+    constexpr int kUW = (MG == 1 && VMODE == 0) ? SPMM_MERGE_WIDE_UNROLL : 2;
+    constexpr int UW = U < kUW ? U : kUW;
     extern __shared__ __align__(128) unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* wb = smem + w * Lay::kWarp;
@@ -808,7 +824,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, VMODE ? 3 : SPMM_MIN_BLOC
     }
 }
 
-template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, bool MG = false>
+template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, int MG = 0>
 cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     using Lay = Layout<VMODE>;
     // per instantiation, computed once (thread-safe; a failure is reported to
@@ -839,7 +855,7 @@ cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <typename XT, bool ONE, bool MG = false>
+template <typename XT, bool ONE, int MG = 0>
 cudaError_t launch_rows_t(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
     static_assert(!(ONE && MG), "one lane per row has no lane groups");
     if (a.n_tasks <= 0) return cudaSuccess;
@@ -847,7 +863,9 @@ cudaError_t launch_rows_t(const FwdArgs& a, int vmode, int vec, int ch, cudaStre
     if (vmode == VM && vec == V && ch == C)                                              \
         return a.compensated ? launch_one<XT, VM, V, C, true, ONE, MG>(a, s)             \
                              : launch_one<XT, VM, V, C, false, ONE, MG>(a, s);
-    if constexpr (MG) {          // CH == 1, at most 4 elements per lane
+    if constexpr (MG == 2) {     // float pattern rows of 4-element lanes only
+        if constexpr (sizeof(XT) == 4) { SPMM_LAUNCH(0, 4, 1) }
+    } else if constexpr (MG == 1) {   // CH == 1, at most 4 elements per lane
         if constexpr (sizeof(XT) == 4) {
             SPMM_LAUNCH(0, 4, 1) SPMM_LAUNCH(0, 2, 1) SPMM_LAUNCH(0, 1, 1)
             SPMM_LAUNCH(1, 4, 1) SPMM_LAUNCH(1, 2, 1) SPMM_LAUNCH(1, 1, 1)

@@ -81,6 +81,17 @@ typedef enum {
  *              rounding error recovered with an FMA) and split rows'
  *              segment partials are combined the same way; 0 = plain
  *              float32 sums (default)
+ *   short_runs  how lane groups share a run of short rows when an X row
+ *              takes several lanes of at most 4 elements (k = 4, 16, 32,
+ *              64 FP32; k = 8 BF16/FP16): 1 = each group sums whole rows
+ *              in turn, 2 = the run's nonzeros are cut into equal pieces,
+ *              one per group, and rows crossing pieces are joined in a
+ *              fixed order; 0 or any other value = automatic: pieces when
+ *              the plan's row-walk efficiency for this many lane groups
+ *              (spmm_info.walk_eff) is below 0.5 and the row is on 4 or
+ *              more lanes or its lanes hold at most 8 bytes, else whole
+ *              rows.  Per orientation, like the plan.  Results differ
+ *              between 1 and 2 only in the order of float32 additions.
  */
 typedef struct {
     int32_t task_nnz;
@@ -91,6 +102,7 @@ typedef struct {
     int32_t stream_slot_kib;
     int32_t debug_fail_block;
     int32_t compensated;
+    int32_t short_runs;
 } spmm_opts;
 
 /* Plan statistics reported by spmm_get_info. */
@@ -107,6 +119,17 @@ typedef struct {
     int32_t has_transpose;
     int32_t n_graphs;            /* graphs in a batched handle (1 otherwise)        */
     int32_t reserved;
+    /* Row-walk efficiency of the forward plan's short-row runs for 2, 4, 8
+     * and 16 lane groups per warp (X rows on 16, 8, 4 and 2 lanes): group g
+     * takes rows g, g+G, ... of a run, one round is one row per group and
+     * lasts as long as its longest row (in batches of 4 nonzeros, at least
+     * one), and the efficiency is the batches summed over the batches the
+     * rounds take (G x the longest); 1 if the plan has no short-row runs.
+     * Low values mean idle groups, which equal pieces per group avoid
+     * (spmm_opts.short_runs).  walk_eff_t: the same for the transposed plan
+     * (or 0). */
+    double walk_eff[4];
+    double walk_eff_t[4];
 } spmm_info;
 
 /*
@@ -372,6 +395,21 @@ int spmm_debug_wait_timeout(uint64_t wait_ns, void* stream);
  */
 int spmm_plan_tasks(int64_t n_rows, const int64_t* row_ptr, const spmm_opts* opts, int32_t* tasks,
                     int64_t* n_tasks, int64_t* n_split_rows, int64_t* n_segments);
+
+/*
+ * spmm_plan_walk_eff -- host-only: the row-walk efficiency of the plan that
+ * spmm_plan_tasks builds (spmm_info.walk_eff: for 2, 4, 8, 16 lane groups),
+ * the statistic the automatic short_runs choice reads.  Section 3.4 balances
+ * work over threads with small batches of rows; this measures how evenly a
+ * run of short rows spreads over the lane groups of a warp when each group
+ * takes whole rows.
+ *   row_ptr   n_rows+1 int64 (host)
+ *   opts      tuning knobs or NULL
+ *   walk_eff  out: 4 doubles
+ * Errors: SPMM_ERR_ARG (null pointer, bad n_rows), SPMM_ERR_FORMAT (row_ptr
+ * not monotone or row_ptr[0] != 0), SPMM_ERR_OOM.
+ */
+int spmm_plan_walk_eff(int64_t n_rows, const int64_t* row_ptr, const spmm_opts* opts, double* walk_eff);
 
 /*
  * spmm_apply_csr_static -- Y = A X without allocating device memory.  The

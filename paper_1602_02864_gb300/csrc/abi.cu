@@ -78,8 +78,10 @@ static int build_orientation(DevCSR& d, int64_t n_rows, int64_t n_cols, const in
                              bool reorder, cudaStream_t s, int64_t* bytes) {
     d.n_rows = n_rows;
     d.n_cols = n_cols;
+    d.short_runs = p.short_runs;
     d.nnz = row_ptr[n_rows];
     HostPlan plan = build_plan(row_ptr, n_rows, p);
+    std::copy(plan.walk_eff, plan.walk_eff + 4, d.walk_eff);
     cudaError_t e;
     if ((e = upload(&d.row_ptr, row_ptr, (size_t)n_rows + 1, 2, s, bytes)) != cudaSuccess)
         return cuda_fail(e, "row_ptr");
@@ -147,6 +149,7 @@ static Params resolve_params(const spmm_opts* opts) {
         if (opts->stream_slot_kib > 0) prm.slot_bytes = (int64_t)opts->stream_slot_kib << 10;
         if (opts->debug_fail_block > 0) prm.fail_block = opts->debug_fail_block;
         prm.compensated = opts->compensated ? 1 : 0;
+        prm.short_runs = (opts->short_runs == 1 || opts->short_runs == 2) ? opts->short_runs : 0;
     }
     prm.task_nnz = std::min(std::max(prm.task_nnz, 32), kMaxTaskNnz);
     prm.task_rows = std::min(std::max(prm.task_rows, 1), kMaxTaskRows);
@@ -183,6 +186,24 @@ extern "C" int spmm_plan_tasks(int64_t n_rows, const int64_t* row_ptr, const spm
     *n_tasks = nt;
     if (n_split_rows) *n_split_rows = (int64_t)plan.splits.size();
     if (n_segments) *n_segments = plan.n_segments;
+    return SPMM_OK;
+}
+
+extern "C" int spmm_plan_walk_eff(int64_t n_rows, const int64_t* row_ptr, const spmm_opts* opts, double* walk_eff) {
+    if (!row_ptr || !walk_eff || n_rows < 0 || n_rows >= (int64_t)1 << 31) {
+        set_error("spmm_plan_walk_eff: bad argument");
+        return SPMM_ERR_ARG;
+    }
+    if (row_ptr[0] != 0) { set_error("spmm_plan_walk_eff: row_ptr[0] != 0"); return SPMM_ERR_FORMAT; }
+    for (int64_t i = 0; i < n_rows; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) { set_error("spmm_plan_walk_eff: row_ptr decreases"); return SPMM_ERR_FORMAT; }
+    try {
+        const HostPlan plan = build_plan(row_ptr, n_rows, resolve_params(opts));
+        std::copy(plan.walk_eff, plan.walk_eff + 4, walk_eff);
+    } catch (const std::bad_alloc&) {
+        set_error("spmm_plan_walk_eff: out of host memory");
+        return SPMM_ERR_OOM;
+    }
     return SPMM_OK;
 }
 
@@ -540,7 +561,7 @@ unsigned long long* task_counter(const DevCSR& d, int32_t k, int32_t xtype, cuda
 }
 
 void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xtype, const float* Y, int64_t ldy,
-                  int* vec_out, int* ch_out) {
+                  const DevCSR& d, int* vec_out, int* ch_out) {
     const int esize = (int)dtype_size(xtype);
     const uintptr_t xa = (uintptr_t)X, ya = (uintptr_t)Y;
     int vec = 16 / esize;
@@ -571,7 +592,11 @@ void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xty
     // FP32: k = 4 1.87 -> 1.79 ms, k = 16 3.27 -> 2.98, k = 32 4.52 -> 4.18),
     // slower for 32-byte rows on two lanes (k = 8 2.21 -> 2.33); lanes of 8
     // 16-bit elements spill in that path and keep the row walk
-    a.merge_groups = ch == 1 && lg >= 1 && vec <= 4 && (lg >= 2 || vec * esize <= 8);
+    const bool pieces_ok = ch == 1 && lg >= 1 && lg <= 4 && vec <= 4;
+    a.merge_groups = d.short_runs == 2 ? pieces_ok
+                     : d.short_runs == 1 ? false
+                                         : pieces_ok && (lg >= 2 || vec * esize <= 8) &&
+                                               d.walk_eff[4 - lg] < kPiecesBelowWalkEff;
     *vec_out = vec;
     *ch_out = ch;
 }
@@ -612,7 +637,7 @@ int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int3
     }
     FwdArgs a;
     int vec = 1, ch = 1;
-    set_geometry(a, X, ldx, k, xtype, Y, ldy, &vec, &ch);
+    set_geometry(a, X, ldx, k, xtype, Y, ldy, d, &vec, &ch);
     cudaError_t ec = cudaSuccess;
     a.task_ctr = task_counter(d, k, xtype, s, &ec, &a.task_chunk);
     if (ec != cudaSuccess) return cuda_fail(ec, "spmm_apply: task counter");
@@ -674,6 +699,10 @@ extern "C" int spmm_get_info(spmm_mat_t A, spmm_info* info) {
     info->value_dtype = A->vtype;
     info->has_transpose = A->has_tr ? 1 : 0;
     info->n_graphs = (int32_t)(A->row_off.size() - 1);
+    for (int i = 0; i < 4; ++i) {
+        info->walk_eff[i] = A->fwd.walk_eff[i];
+        info->walk_eff_t[i] = A->has_tr ? A->tr.walk_eff[i] : 0.0;
+    }
     return SPMM_OK;
 }
 
@@ -733,6 +762,7 @@ namespace spmm {
 // Rebuild the task plan of one orientation for new parameters; the matrix
 // itself stays where it is.
 static int replan_orientation(DevCSR& d, const Params& p, cudaStream_t s, int64_t* bytes) {
+    d.short_runs = p.short_runs;
     std::vector<int64_t> rp;
     try {
         rp.resize((size_t)d.n_rows + 1);
@@ -773,6 +803,7 @@ static int replan_orientation(DevCSR& d, const Params& p, cudaStream_t s, int64_
     d.n_segments = plan.n_segments;
     d.partials = partials;
     d.n_slots = plan.n_slots;
+    std::copy(plan.walk_eff, plan.walk_eff + 4, d.walk_eff);
     return SPMM_OK;
 }
 

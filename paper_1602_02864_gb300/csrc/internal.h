@@ -38,6 +38,9 @@ struct HostPlan {
     int64_t n_slots = 0;
     int64_t n_segments = 0;
     int64_t n_short = 0, n_long = 0;
+    // row-walk efficiency of the short-row runs for 2, 4, 8, 16 lane groups
+    // (spmm_info.walk_eff)
+    double walk_eff[4] = {1.0, 1.0, 1.0, 1.0};
 };
 
 // Device-side copy of one orientation (CSR of A, or CSR of A^T == CSC of A).
@@ -56,6 +59,8 @@ struct DevCSR {
     int64_t n_slots = 0;
     int32_t* perm = nullptr;        // SPMM_REORDER: original index of relabelled column c (n_cols)
     unsigned long long* task_ctr = nullptr;   // task counter of dynamically scheduled launches
+    int32_t short_runs = 0;         // short-row runs over lane groups (spmm_opts.short_runs)
+    double walk_eff[4] = {1.0, 1.0, 1.0, 1.0};   // HostPlan::walk_eff of the current plan
 };
 
 // Streaming mode: the matrix stays in (pinned) host memory and flows to HBM
@@ -108,6 +113,7 @@ struct Params {
     int64_t slot_bytes = 256ll << 20;   // streaming staging slot (column indices)
     int32_t fail_block = 0;
     int32_t compensated = 0;            // compensated sums for long rows and hub segments
+    int32_t short_runs = 0;             // 0 automatic, 1 row walk, 2 pieces per lane group
 };
 
 }  // namespace spmm
@@ -176,7 +182,9 @@ unsigned long long* task_counter(const DevCSR& d, int32_t k, int32_t xtype, cuda
                                  int32_t* chunk);
 struct FwdArgs;
 void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xtype, const float* Y, int64_t ldy,
-                  int* vec_out, int* ch_out);
+                  const DevCSR& d, int* vec_out, int* ch_out);
+// automatic short_runs: pieces per lane group below this row-walk efficiency
+constexpr double kPiecesBelowWalkEff = 0.5;
 int value_mode(const spmm_mat* A, int32_t xtype);
 cudaError_t launch_rows(const FwdArgs& a, int32_t xtype, int vmode, int vec, int ch, cudaStream_t s);
 

@@ -26,6 +26,32 @@ static int4 desc(int64_t r0, int32_t x, int64_t e0) {
     return make_int4((int)r0, x, (int)(uint32_t)(e0 & 0xffffffffll), (int)(e0 >> 32));
 }
 
+// Row-walk efficiency of the short-row runs for G = 2, 4, 8, 16 lane groups:
+// in a run, group g takes rows g, g+G, ...; a round (one row per group) lasts
+// as long as its longest row, counted in batches of 4 nonzeros (the gathers a
+// group keeps in flight) and at least one.  The efficiency is the batches of
+// all rounds over G x the longest of each round.
+static void walk_efficiency(const int64_t* row_ptr, HostPlan& plan) {
+    double done[4] = {0, 0, 0, 0}, taken[4] = {0, 0, 0, 0};
+    for (size_t t = 0; t + 1 < plan.tasks.size(); ++t) {
+        const int4 d = plan.tasks[t];
+        if (d.y < 1) continue;
+        for (int gi = 0; gi < 4; ++gi) {
+            const int G = 2 << gi;
+            for (int j = 0; j < d.y; j += G) {
+                int64_t mx = 1;
+                for (int q = j; q < std::min(j + G, d.y); ++q) {
+                    const int64_t b = (row_ptr[d.x + q + 1] - row_ptr[d.x + q] + 3) / 4;
+                    done[gi] += (double)b;
+                    mx = std::max(mx, b);
+                }
+                taken[gi] += (double)G * (double)mx;
+            }
+        }
+    }
+    for (int gi = 0; gi < 4; ++gi) plan.walk_eff[gi] = taken[gi] > 0 ? done[gi] / taken[gi] : 1.0;
+}
+
 HostPlan build_plan(const int64_t* row_ptr, int64_t n_rows, const Params& p) {
     HostPlan plan;
     const int64_t T = p.task_nnz, R = p.task_rows, LR = p.long_row, SM = p.short_max;
@@ -61,6 +87,7 @@ HostPlan build_plan(const int64_t* row_ptr, int64_t n_rows, const Params& p) {
         ++plan.n_short;
     }
     plan.tasks.push_back(desc(n_rows, 0, row_ptr[n_rows]));   // sentinel
+    walk_efficiency(row_ptr, plan);
     return plan;
 }
 

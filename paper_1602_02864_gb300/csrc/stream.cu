@@ -87,6 +87,8 @@ int stream_setup(spmm_mat* A, const int64_t* row_ptr, const int32_t* col_idx, co
     S.h_val = values;
     S.fail_block = A->params.fail_block;
     HostPlan plan = build_plan(row_ptr, n, A->params);
+    d.short_runs = A->params.short_runs;
+    std::copy(plan.walk_eff, plan.walk_eff + 4, d.walk_eff);
     const int64_t slot_nnz = std::max<int64_t>(A->params.slot_bytes / 4, 2 * kMaxTaskNnz + 16);
     int64_t max_nnz = 0, max_rows = 0;
     cut_blocks(plan.tasks, n, slot_nnz, S.blocks, &max_nnz, &max_rows);
@@ -188,7 +190,7 @@ int stream_apply(const spmm_mat* A, const void* X, int64_t ldx, int32_t k, int32
     const size_t vsize = vmode == 0 ? 0 : (vmode == 1 ? 4 : 2);
     FwdArgs a;
     int vec = 1, ch = 1;
-    set_geometry(a, X, ldx, k, xtype, Y, ldy, &vec, &ch);
+    set_geometry(a, X, ldx, k, xtype, Y, ldy, d, &vec, &ch);
     a.partials = d.partials;
     a.status = A->status;
     a.wait_ns = kWaitNs;

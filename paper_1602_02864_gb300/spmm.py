@@ -40,7 +40,8 @@ class SpmmError(RuntimeError):
 class spmm_opts(ctypes.Structure):
     _fields_ = [("task_nnz", ctypes.c_int32), ("task_rows", ctypes.c_int32), ("long_row", ctypes.c_int32),
                 ("short_max", ctypes.c_int32), ("x_l2_policy", ctypes.c_int32), ("stream_slot_kib", ctypes.c_int32),
-                ("debug_fail_block", ctypes.c_int32), ("compensated", ctypes.c_int32)]
+                ("debug_fail_block", ctypes.c_int32), ("compensated", ctypes.c_int32),
+                ("short_runs", ctypes.c_int32)]
 
 
 class spmm_tile_desc(ctypes.Structure):
@@ -52,7 +53,7 @@ class spmm_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("n_rows", "n_cols", "nnz", "n_tasks", "n_split_rows", "n_segments",
                                               "n_tasks_t", "n_split_rows_t", "n_segments_t", "device_bytes")] + [
         ("value_dtype", ctypes.c_int32), ("has_transpose", ctypes.c_int32), ("n_graphs", ctypes.c_int32),
-        ("reserved", ctypes.c_int32)]
+        ("reserved", ctypes.c_int32), ("walk_eff", ctypes.c_double * 4), ("walk_eff_t", ctypes.c_double * 4)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -79,6 +80,8 @@ _lib.spmm_debug_wait_timeout.restype = ctypes.c_int
 _lib.spmm_plan_tasks.argtypes = [_i64, _P, ctypes.POINTER(spmm_opts), _P, ctypes.POINTER(_i64),
                                  ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
 _lib.spmm_plan_tasks.restype = ctypes.c_int
+_lib.spmm_plan_walk_eff.argtypes = [_i64, _P, ctypes.POINTER(spmm_opts), ctypes.POINTER(ctypes.c_double)]
+_lib.spmm_plan_walk_eff.restype = ctypes.c_int
 _lib.spmm_apply_csr_static.argtypes = [_i64, _i64, _i64, _P, _P, _P, ctypes.c_int, _P, _i64, _i64, _P, _i64,
                                        _i32, ctypes.c_int, _P, _i64, _P]
 _lib.spmm_apply_csr_static.restype = ctypes.c_int
@@ -219,6 +222,15 @@ def spmm_plan_tasks(row_ptr, opts: spmm_opts | None = None):
     _check(_lib.spmm_plan_tasks(n_rows, _ptr(rp), o, _ptr(tasks), ctypes.byref(nt), ctypes.byref(ns),
                                 ctypes.byref(nseg)))
     return tasks, ns.value, nseg.value
+
+
+def spmm_plan_walk_eff(row_ptr, opts: spmm_opts | None = None) -> list[float]:
+    """Host-only row-walk efficiency of the plan for 2, 4, 8, 16 lane groups."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    out = (ctypes.c_double * 4)()
+    o = ctypes.byref(opts) if opts is not None else None
+    _check(_lib.spmm_plan_walk_eff(len(rp) - 1, _ptr(rp), o, out))
+    return list(out)
 
 
 def spmm_apply_csr_static(n_rows, n_cols, nnz, row_ptr, col_idx, values, vtype, tasks, n_tasks, n_segments, X,
@@ -434,7 +446,10 @@ def spmm_svds(h, nsv, V0, block=16, max_basis=64, max_restarts=100, tol=1e-6, xt
 def spmm_get_info(h) -> dict:
     info = spmm_info()
     _check(_lib.spmm_get_info(h, ctypes.byref(info)))
-    return {name: getattr(info, name) for name, _ in info._fields_}
+    out = {name: getattr(info, name) for name, _ in info._fields_}
+    out["walk_eff"] = list(info.walk_eff)
+    out["walk_eff_t"] = list(info.walk_eff_t)
+    return out
 
 
 def spmm_destroy(h):

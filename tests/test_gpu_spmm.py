@@ -132,14 +132,16 @@ def test_plan_shapes_agree(sp, opts):
 
 @pytest.mark.parametrize("kind", ["uniform", "geometric", "bimodal", "sparse"])
 @pytest.mark.parametrize("task_nnz", [32, 100, 512])
-def test_merge_rows_cross_lane_pieces(sp, kind, task_nnz):
+@pytest.mark.parametrize("short_runs", [0, 1, 2])
+def test_merge_rows_cross_lane_pieces(sp, kind, task_nnz, short_runs):
     """One lane per X row (k = 2 in FP32, k = 2 and 4 in BF16) cuts each
     short-row run into 32 equal pieces of nonzeros, and rows on several lanes
     of at most 4 elements (k = 4, 16, 32, 64 in FP32; 8, 16, 32 in BF16 and
     FP16) cut it into one piece per lane group; rows that start before a
     piece, span several pieces or have no nonzeros must all come out right.
     Degree mixes: uniform 0..63, geometric, mostly 0..2 with 10% of 30..63,
-    and 0/1."""
+    and 0/1.  short_runs 1 and 2 force whole rows or pieces per lane group
+    where the automatic choice (0) would take the other."""
     import torch
     rng = np.random.default_rng({"uniform": 1, "geometric": 2, "bimodal": 3, "sparse": 4}[kind])
     n = 3000
@@ -151,7 +153,7 @@ def test_merge_rows_cross_lane_pieces(sp, kind, task_nnz):
     src = np.repeat(np.arange(n), deg)
     dst = np.concatenate([rng.choice(n, d, replace=False) for d in deg]) if deg.sum() else np.zeros(0, int)
     A = graphs.csr_from_edges(n, n, src, dst, rng.random(len(src)).astype(np.float32))
-    o = sp.spmm_opts(task_nnz=task_nnz, task_rows=64, long_row=512, short_max=63)
+    o = sp.spmm_opts(task_nnz=task_nnz, task_rows=64, long_row=512, short_max=63, short_runs=short_runs)
     hp = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, transpose=True, opts=o)
     hw = sp.SparseMatrix.from_csr(A, transpose=True, opts=o)
     for tr in (False, True):
@@ -273,3 +275,20 @@ def test_bounded_wait_times_out_and_context_survives(sp, rmat16, rmat16_handles)
     hp.sync_status()
     ref = oracle.spmm(rmat16.n_rows, rmat16.n_cols, rmat16.row_ptr, rmat16.col_idx, None, X)
     assert np.array_equal(Y, ref)
+
+
+def test_info_walk_eff_matches_host_plan(sp):
+    """The handle's row-walk efficiency (which the automatic short_runs
+    choice reads) is the host plan's, for both orientations and after a
+    replan."""
+    A = synth.rmat_csr(14, seed=4)
+    o = sp.spmm_opts(task_nnz=256, short_max=31)
+    h = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, transpose=True, opts=o)
+    rpt = np.concatenate([[0], np.cumsum(np.bincount(A.col_idx, minlength=A.n_cols))]).astype(np.int64)
+    info = h.info()
+    assert info["walk_eff"] == sp.spmm_plan_walk_eff(A.row_ptr, o)
+    assert info["walk_eff_t"] == sp.spmm_plan_walk_eff(rpt, o)
+    o2 = sp.spmm_opts(task_nnz=512, short_max=63)
+    sp.spmm_replan(h.handle, o2, 0)
+    assert h.info()["walk_eff"] == sp.spmm_plan_walk_eff(A.row_ptr, o2)
+    h.close()

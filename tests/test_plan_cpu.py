@@ -124,3 +124,71 @@ def test_plan_invariants_random_degrees(sp):
             assert len(lens) >= 2 and len(set(lens[:-1])) == 1 and lens[-1] <= lens[0]
 
     prop()
+
+
+def walk_eff_by_definition(sp, rp, opts=None):
+    """Row-walk efficiency written out from its definition in spmm.h over the
+    plan's short-row tasks: per round of G consecutive rows of a task, the
+    batches of 4 nonzeros summed, over G x the longest (at least 1)."""
+    tasks, _, _ = sp.spmm_plan_tasks(rp, opts)
+    deg = np.diff(rp)
+    out = []
+    for G in (2, 4, 8, 16):
+        done = taken = 0
+        for t in range(len(tasks) - 1):
+            r0, x = int(tasks[t, 0]), int(tasks[t, 1])
+            if x < 1:
+                continue
+            for j in range(0, x, G):
+                b = [(int(deg[r0 + q]) + 3) // 4 for q in range(j, min(j + G, x))]
+                done += sum(b)
+                taken += G * max(1, max(b))
+        out.append(done / taken if taken else 1.0)
+    return out
+
+
+def test_walk_eff_closed_forms(sp):
+    # one row of 4 nonzeros and three empty rows: one batch done per round
+    # of G groups (two rounds at G = 2)
+    assert sp.spmm_plan_walk_eff(np.array([0, 4, 4, 4, 4])) == [0.25, 0.25, 0.125, 0.0625]
+    # 64 rows of 8 nonzeros: every round is full
+    assert sp.spmm_plan_walk_eff(np.arange(65, dtype=np.int64) * 8) == [1.0, 1.0, 1.0, 1.0]
+    # only long rows (no short-row runs): 1 by definition
+    assert sp.spmm_plan_walk_eff(np.array([0, 100, 300], dtype=np.int64)) == [1.0, 1.0, 1.0, 1.0]
+    # rows of 1 and 5 nonzeros alternating: batches 1, 2; at G = 2 each
+    # round does 3 of 4; wider rounds hold both lengths too
+    rp = np.concatenate([[0], np.cumsum(np.tile([1, 5], 32))]).astype(np.int64)
+    assert sp.spmm_plan_walk_eff(rp) == [0.75, 0.75, 0.75, 0.75]
+    # empty matrix
+    assert sp.spmm_plan_walk_eff(np.zeros(1, dtype=np.int64)) == [1.0, 1.0, 1.0, 1.0]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_walk_eff_matches_definition(sp, seed):
+    rng = np.random.default_rng(seed)
+    n = 5000
+    deg = np.where(rng.random(n) < 0.3, 0, rng.geometric(0.08, n))
+    hubs = rng.random(n) < 0.01
+    deg[hubs] = rng.integers(64, 2000, int(hubs.sum()))
+    rp = np.concatenate([[0], np.cumsum(deg)]).astype(np.int64)
+    for o in (None, sp.spmm_opts(task_nnz=128, short_max=31, task_rows=40)):
+        np.testing.assert_allclose(sp.spmm_plan_walk_eff(rp, o), walk_eff_by_definition(sp, rp, o), rtol=1e-12)
+
+
+def test_walk_eff_orders_graph_families(sp):
+    """The automatic short_runs rule reads this statistic: on R-MAT most
+    rounds wait on one long row (efficiency well below 0.5 for 8 and 16
+    groups), on a Chung-Lu batch and an SBM graph rows are closer in length
+    (above 0.5)."""
+    rm = sp.spmm_plan_walk_eff(synth.rmat_csr(16, seed=0).row_ptr)
+    assert rm == sorted(rm, reverse=True) and rm[3] < 0.35 and rm[2] < 0.45
+    for A in (synth.sbm_csr(1 << 16, 16, 16.0, 0.5, seed=0), synth.chunglu_csr(3, seed=0)):
+        e = sp.spmm_plan_walk_eff(A.row_ptr)
+        assert e == sorted(e, reverse=True) and min(e) > 0.5, e
+
+
+def test_walk_eff_rejects_bad_row_ptr(sp):
+    with pytest.raises(sp.SpmmError):
+        sp.spmm_plan_walk_eff(np.array([1, 2, 3], dtype=np.int64))
+    with pytest.raises(sp.SpmmError):
+        sp.spmm_plan_walk_eff(np.array([0, 5, 3], dtype=np.int64))

@@ -23,7 +23,8 @@ namespace spmm {
 constexpr int kWarpsPerBlock = 8;
 constexpr int kMaxTaskNnz = 512;    // staged nonzeros per task (shared memory)
 constexpr int kMaxTaskRows = 64;    // rows per short-row task
-constexpr int kSlotStride = 64;     // floats per partial-result slot (k <= 64)
+constexpr int kSlotStride = 64;     // floats allocated per partial-result slot (k <= 64; a call
+                                    // with k columns packs slot s at s * k)
 constexpr int kMaxK = 64;
 constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every device-side staging wait (2 s)
 // per-warp staging buffer (one of two): column indices, values, row pointers,
@@ -54,7 +55,7 @@ struct DevCSR {
     int4* splits = nullptr;
     int64_t n_splits = 0;
     int64_t n_segments = 0;
-    float* partials = nullptr;      // scratch: n_slots x kSlotStride floats
+    float* partials = nullptr;      // scratch: n_slots x kSlotStride floats (slot s of a k-column call at s * k)
     float* partials_comp = nullptr; // compensation terms of the partials (compensated plans only)
     int64_t n_slots = 0;
     int32_t* perm = nullptr;        // SPMM_REORDER: original index of relabelled column c (n_cols)

@@ -763,7 +763,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
                         for (int c = 0; c < CH; ++c)
                             if (act[c]) store_y<VEC>(dst + (li + c * LANES) * VEC, acc[c]);
                     } else {                           // segment: keep the pair for the combine pass
-                        const int64_t slot = (int64_t)(-d0.y - 1) * kSlotStride;
+                        const int64_t slot = (int64_t)(-d0.y - 1) * a.k;
 #pragma unroll
                         for (int c = 0; c < CH; ++c)
                             if (act[c]) {
@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
                         for (int v = 0; v < VEC; ++v) acc[c][v] += __shfl_xor_sync(0xffffffffu, acc[c][v], off);
                 if (g == 0) {
                     float* dst = (d0.y == 0) ? a.Y + (int64_t)d0.x * a.ldy
-                                             : a.partials + (int64_t)(-d0.y - 1) * kSlotStride;
+                                             : a.partials + (int64_t)(-d0.y - 1) * a.k;
 #pragma unroll
                     for (int c = 0; c < CH; ++c)
                         if (act[c]) store_y<VEC>(dst + (li + c * LANES) * VEC, acc[c]);

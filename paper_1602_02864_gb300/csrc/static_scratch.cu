@@ -68,7 +68,7 @@ combine_from_tasks_kernel(const int4* __restrict__ tasks, int64_t n_tasks, const
     const int64_t last = -(int64_t)d.y - 1, first = last - before;
     for (int c = lane; c < k; c += 32) {
         float acc = 0.f;
-        for (int64_t q = first; q <= last; ++q) acc += __ldcg(partials + q * kSlotStride + c);
+        for (int64_t q = first; q <= last; ++q) acc += __ldcg(partials + q * k + c);
         Y[(int64_t)d.x * ldy + c] = acc;
     }
 }

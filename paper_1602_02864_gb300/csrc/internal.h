@@ -252,7 +252,7 @@ cudaError_t launch_rows_f32_mg(const FwdArgs& a, int vmode, int vec, int ch, cud
 cudaError_t launch_rows_bf16_mg(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
 cudaError_t launch_rows_f16_mg(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
 
-// combine.cu: Y[row] = sum of the split row's partials in segment order.
+// combine.cu: Y[row] = sum of the split row's partials in a fixed order.
 cudaError_t launch_combine(const int4* splits, int64_t n_splits, const float* partials, float* Y,
                            int64_t ldy, int32_t k, cudaStream_t s, const float* partials_comp = nullptr);
 

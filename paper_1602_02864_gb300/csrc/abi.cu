@@ -587,11 +587,14 @@ void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xty
     a.k = k;
     a.lanes_log2 = lg;
     a.nvec = nvec;
-    // merge-based short-row runs over lane groups measured faster for rows
-    // on 4 or more lanes and for lanes of at most 8 bytes (R-MAT scale 24,
-    // FP32: k = 4 1.87 -> 1.79 ms, k = 16 3.27 -> 2.98, k = 32 4.52 -> 4.18),
-    // slower for 32-byte rows on two lanes (k = 8 2.21 -> 2.33); lanes of 8
-    // 16-bit elements spill in that path and keep the row walk
+    // Short-row runs over lane groups: equal pieces per group (merge_groups)
+    // or whole rows per group.  Pieces win where the row walk would leave
+    // groups idle behind the longest row of each round (plan statistic
+    // walk_eff below 0.5: R-MAT, FP32 k = 16 2.79 -> 2.70 ms, k = 32
+    // 4.38 -> 4.18) and lose where rows have similar lengths (Chung-Lu batch
+    // k = 16 0.88 -> 1.19 ms, SBM k = 64 10.9 -> 13.0).  32-byte rows on two
+    // lanes keep the walk (R-MAT k = 8 2.21 -> 2.33 with pieces); lanes of 8
+    // 16-bit elements spill in the pieces path, which is not built for them.
     const bool pieces_ok = ch == 1 && lg >= 1 && lg <= 4 && vec <= 4;
     a.merge_groups = d.short_runs == 2 ? pieces_ok
                      : d.short_runs == 1 ? false

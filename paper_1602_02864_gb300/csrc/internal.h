@@ -234,9 +234,14 @@ struct FwdArgs {
 // k = 16 3.97 -> 3.22 ms against the static stride).  Narrow-row tasks are
 // short, and claiming them one at a time made the counter's atomics the
 // bottleneck (k = 1 1.11 -> 1.38 ms), so they are claimed kNarrowTaskChunk at
-// a time (k = 1 on A^T 1.15 -> 1.11 ms, 30 PageRank iterations 40.5 -> 38.0 ms).
+// a time.  With three blocks per SM, 30 PageRank iterations took 34.4 / 30.8 /
+// 30.0 / 30.2 / 30.5 ms claiming 2 / 4 / 8 / 16 / 32 tasks (BF16 k = 1 1.08 /
+// 0.94 / 0.89 / 0.88 / 0.89 ms).
 constexpr int kWideRowBytes = 16;
-constexpr int kNarrowTaskChunk = 4;
+#ifndef SPMM_NARROW_TASK_CHUNK
+#define SPMM_NARROW_TASK_CHUNK 8
+#endif
+constexpr int kNarrowTaskChunk = SPMM_NARROW_TASK_CHUNK;
 
 // rows_*.cu: launch the task kernel for one X dtype.  vmode: 0 pattern,
 // 1 f32 values, 2 bf16 values, 3 f16 values.  Returns a cudaError_t.

@@ -765,7 +765,6 @@ namespace spmm {
 // Rebuild the task plan of one orientation for new parameters; the matrix
 // itself stays where it is.
 static int replan_orientation(DevCSR& d, const Params& p, cudaStream_t s, int64_t* bytes) {
-    d.short_runs = p.short_runs;
     std::vector<int64_t> rp;
     try {
         rp.resize((size_t)d.n_rows + 1);
@@ -807,6 +806,7 @@ static int replan_orientation(DevCSR& d, const Params& p, cudaStream_t s, int64_
     d.partials = partials;
     d.n_slots = plan.n_slots;
     std::copy(plan.walk_eff, plan.walk_eff + 4, d.walk_eff);
+    d.short_runs = p.short_runs;
     return SPMM_OK;
 }
 

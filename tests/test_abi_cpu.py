@@ -62,3 +62,39 @@ def test_host_validation_without_gpu(lib):
                              None)
     assert rc == sp.SPMM_ERR_ARG
     assert lib.spmm_destroy(None) == 0
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the header's layout: a C
+    program compiled against include/spmm.h prints every field's offset and
+    size and each struct's size, and the binding must agree."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_1602_02864_gb300 import spmm as sp
+    structs = {"spmm_opts": sp.spmm_opts, "spmm_info": sp.spmm_info, "spmm_tile_desc": sp.spmm_tile_desc}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "spmm.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'    printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{name} {field} %zu %zu\\n", offsetof({name}, {field}), '
+                         f'sizeof((({name}*)0)->{field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c = {}
+    for line in out:
+        if line:
+            parts = line.split()
+            c[tuple(parts[:-2] if parts[1] != "sizeof" else parts[:2])] = tuple(int(x) for x in parts[-2:]) \
+                if parts[1] != "sizeof" else int(parts[2])
+    for name, cls in structs.items():
+        assert c[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            f = getattr(cls, field)
+            assert c[(name, field)] == (f.offset, f.size), (name, field)

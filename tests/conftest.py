@@ -14,7 +14,7 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    # GPU tests must run on a GPU machine; skip them (not fail) when no GPU is visible
+    # GPU tests need a visible GPU; skip them (not fail) when there is none
     # unless the run asked for them explicitly with -m gpu.
     try:
         import torch

@@ -433,14 +433,21 @@ int spmm_plan_walk_eff(int64_t n_rows, const int64_t* row_ptr, const spmm_opts* 
  *   n_tasks, n_segments   as returned by spmm_plan_tasks; at most 16384
  *             segments (split hub-row pieces) fit the static scratch
  *   X, ldx, k, xtype, Y, ldy   as for spmm_apply (Y float32, device)
- * The result equals spmm_apply on a handle created from the same matrix and
- * options.  The first call on a device looks up the static array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call shares the array and it keeps
- * the last call's contents: calls whose work overlaps on the GPU race, so
- * order them on one stream or synchronise between them.  The status word is
- * cleared by each call; a timed-out staging wait leaves Y incomplete and is
- * not reported by this entry point.  Asynchronous on `stream`.
+ * The result matches spmm_apply on a handle created from the same matrix and
+ * options within the tolerances of spmm_apply (bit for bit where every
+ * partial sum is exact): both use the same task kernel and lane geometry,
+ * but this entry point always walks short rows whole per lane group and
+ * never compensates, so rows spread over several lanes may be summed in
+ * another order.  The first call on a device looks up the static array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call shares the array and it
+ * keeps the last call's contents: calls whose work overlaps on the GPU race,
+ * so order them on one stream or synchronise between them.  Each call clears
+ * the array's status word; a timed-out staging wait, or a task whose
+ * partial-sum slot lies beyond the 16384 slots (a task list that does not
+ * belong to row_ptr), sets it and leaves part of Y unwritten -- the kernels
+ * never write outside the array.  spmm_static_status reports it.
+ * Asynchronous on `stream`.
  * Errors: SPMM_ERR_ARG (sizes, NULL, more than 16384 segments),
  * SPMM_ERR_UNSUPPORTED (value/X type mix), SPMM_ERR_CUDA.
  */
@@ -448,6 +455,18 @@ int spmm_apply_csr_static(int64_t n_rows, int64_t n_cols, int64_t nnz, const int
                           const int32_t* col_idx, const void* values, spmm_dtype vtype, const int32_t* tasks,
                           int64_t n_tasks, int64_t n_segments, const void* X, int64_t ldx, int32_t k,
                           spmm_dtype xtype, float* Y, int64_t ldy, void* stream);
+
+/*
+ * spmm_static_status -- the status of the most recent spmm_apply_csr_static
+ * call on the current device, without allocating.  The paper has no
+ * counterpart.  Synchronises `stream` (the stream the call was made on), then
+ * reads the static array's status word with a 4-byte copy into host memory.
+ * Returns SPMM_OK, SPMM_ERR_TIMEOUT (a staging wait ran out: Y incomplete),
+ * SPMM_ERR_FORMAT (the task list named partial-sum slots beyond the static
+ * array: the split rows of Y were not written) or SPMM_ERR_CUDA.  The word is
+ * cleared by the next spmm_apply_csr_static call, not by this query.
+ */
+int spmm_static_status(void* stream);
 
 /*
  * spmm_pagerank -- PageRank by power iteration (Section 4.1):

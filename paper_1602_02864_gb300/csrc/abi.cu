@@ -549,8 +549,7 @@ extern "C" int spmm_create_batched(spmm_mat_t* out, int32_t n_graphs, const int6
 
 namespace spmm {
 
-// Lane geometry of one call: the widest vector that divides k and keeps every
-// X load and Y store aligned, lanes per nonzero and column chunks.
+// The task counter of a launch (reset on s) and the tasks claimed at a time.
 unsigned long long* task_counter(const DevCSR& d, int32_t k, int32_t xtype, cudaStream_t s, cudaError_t* e,
                                  int32_t* chunk) {
     *e = cudaSuccess;
@@ -560,10 +559,10 @@ unsigned long long* task_counter(const DevCSR& d, int32_t k, int32_t xtype, cuda
     return *e == cudaSuccess ? d.task_ctr : nullptr;
 }
 
-void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xtype, const float* Y, int64_t ldy,
-                  const DevCSR& d, int* vec_out, int* ch_out) {
+LaneGeometry lane_geometry(const void* X, int64_t ldx, int32_t k, int32_t xtype, const float* Y, int64_t ldy) {
     const int esize = (int)dtype_size(xtype);
     const uintptr_t xa = (uintptr_t)X, ya = (uintptr_t)Y;
+    LaneGeometry g;
     int vec = 16 / esize;
     for (; vec > 1; vec >>= 1) {
         const int yv = std::min(vec, 4);
@@ -575,11 +574,19 @@ void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xty
     // slower than two lanes of 8 bytes (BF16 k = 8: 2.27 -> 2.08 ms on R-MAT
     // scale 24), so such rows get two lanes.
     if (vec * esize == 16 && k == vec) vec >>= 1;
-    const int nvec = k / vec;
-    const int ch = nvec > 32 ? 2 : 1;
-    const int per = (nvec + ch - 1) / ch;
-    int lg = 0;
-    while ((1 << lg) < per) ++lg;
+    g.vec = vec;
+    g.nvec = k / vec;
+    g.ch = g.nvec > 32 ? 2 : 1;
+    const int per = (g.nvec + g.ch - 1) / g.ch;
+    while ((1 << g.lanes_log2) < per) ++g.lanes_log2;
+    return g;
+}
+
+void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xtype, const float* Y, int64_t ldy,
+                  const DevCSR& d, int* vec_out, int* ch_out) {
+    const int esize = (int)dtype_size(xtype);
+    const LaneGeometry gm = lane_geometry(X, ldx, k, xtype, Y, ldy);
+    const int vec = gm.vec, ch = gm.ch, lg = gm.lanes_log2, nvec = gm.nvec;
     a.X = X;
     a.ldx = ldx;
     a.Y = const_cast<float*>(Y);
@@ -650,6 +657,7 @@ int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int3
     a.tasks = d.tasks;
     a.n_tasks = d.n_tasks;
     a.partials = d.partials;
+    a.n_slots = d.n_slots;
     a.status = A->status;
     a.wait_ns = kWaitNs;
     a.x_evict_last = A->params.x_evict_last;
@@ -733,9 +741,14 @@ extern "C" int spmm_sync_status(spmm_mat_t A, void* stream) {
         return cuda_fail(e, "spmm_sync_status: read status");
     if (st != 0) {
         cudaMemset(A->status, 0, sizeof(int32_t));
-        set_error("spmm_sync_status: a device-side staging wait timed out; results of the calls since the "
-                  "last check are incomplete");
-        return SPMM_ERR_TIMEOUT;
+        if (st & kStatusTimeout) {
+            set_error("spmm_sync_status: a device-side staging wait timed out; results of the calls since the "
+                      "last check are incomplete");
+            return SPMM_ERR_TIMEOUT;
+        }
+        set_error("spmm_sync_status: a task named a partial slot beyond the scratch; results of the calls "
+                  "since the last check are incomplete");
+        return SPMM_ERR_FORMAT;
     }
     return SPMM_OK;
 }

@@ -27,6 +27,9 @@ constexpr int kSlotStride = 64;     // floats allocated per partial-result slot 
                                     // with k columns packs slot s at s * k)
 constexpr int kMaxK = 64;
 constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every device-side staging wait (2 s)
+// bits of the device status word
+constexpr int32_t kStatusTimeout = 1;     // a staging wait ran out; the call's results are incomplete
+constexpr int32_t kStatusSlotRange = 2;   // a task named a partial slot beyond the scratch; its result is missing
 // per-warp staging buffer (one of two): column indices, values, row pointers,
 // each padded for 16-byte aligned bulk copies of an unaligned window
 constexpr int kColBufInts = kMaxTaskNnz + 8;          // 2080 bytes
@@ -182,6 +185,13 @@ int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int3
 unsigned long long* task_counter(const DevCSR& d, int32_t k, int32_t xtype, cudaStream_t s, cudaError_t* e,
                                  int32_t* chunk);
 struct FwdArgs;
+// Lane geometry of one call: VEC elements per lane load (the widest vector
+// that divides k and keeps every X load and Y store aligned), CH column
+// chunks, 2^lanes_log2 lanes per X row, nvec = k / VEC.
+struct LaneGeometry {
+    int vec = 1, ch = 1, lanes_log2 = 0, nvec = 1;
+};
+LaneGeometry lane_geometry(const void* X, int64_t ldx, int32_t k, int32_t xtype, const float* Y, int64_t ldy);
 void set_geometry(FwdArgs& a, const void* X, int64_t ldx, int32_t k, int32_t xtype, const float* Y, int64_t ldy,
                   const DevCSR& d, int* vec_out, int* ch_out);
 // automatic short_runs: pieces per lane group below this row-walk efficiency
@@ -205,6 +215,8 @@ struct FwdArgs {
     const int4* tasks;
     int64_t n_tasks;
     float* partials;
+    int64_t n_slots;      // slots in `partials`: a segment task whose slot is not below this
+                          // writes nothing and sets kStatusSlotRange in *status
     const void* X;
     int64_t ldx;
     float* Y;
@@ -212,7 +224,7 @@ struct FwdArgs {
     int32_t k;
     int32_t lanes_log2;   // log2(lanes per nonzero)
     int32_t nvec;         // k / VEC vectors per X row
-    int32_t* status;      // set to 1 if a staging wait times out
+    int32_t* status;      // status bits (kStatusTimeout, kStatusSlotRange), or-ed in by the kernels
     uint64_t wait_ns;     // bound of every staging wait
     int32_t x_evict_last; // gather X with the L2 evict-last policy
     int32_t compensated;  // long rows / hub segments: compensated summation

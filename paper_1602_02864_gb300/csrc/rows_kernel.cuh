@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
         if (tnn < a.n_tasks) { m0 = a.tasks[tnn]; m1 = a.tasks[tnn + 1]; }
 
         if (!mbar_wait_bounded(&bars[b], (phase >> b) & 1u, a.wait_ns)) {
-            if (lane == 0) atomicExch(a.status, 1);
+            if (lane == 0) atomicOr(a.status, kStatusTimeout);
             if (tn < a.n_tasks) mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u, a.wait_ns);
             return;
         }
@@ -762,7 +762,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
 #pragma unroll
                         for (int c = 0; c < CH; ++c)
                             if (act[c]) store_y<VEC>(dst + (li + c * LANES) * VEC, acc[c]);
-                    } else {                           // segment: keep the pair for the combine pass
+                    } else if ((int64_t)(-d0.y - 1) < a.n_slots) {   // segment: keep the pair for the combine pass
                         const int64_t slot = (int64_t)(-d0.y - 1) * a.k;
 #pragma unroll
                         for (int c = 0; c < CH; ++c)
@@ -770,6 +770,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
                                 store_y<VEC>(a.partials + slot + (li + c * LANES) * VEC, acc[c]);
                                 store_y<VEC>(a.partials_comp + slot + (li + c * LANES) * VEC, cmp[c]);
                             }
+                    } else if (lane == 0) {                // a slot beyond the scratch: write nothing
+                        atomicOr(a.status, kStatusSlotRange);
                     }
                 }
             } else {
@@ -807,7 +809,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
                     for (int c = 0; c < CH; ++c)
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) acc[c][v] += __shfl_xor_sync(0xffffffffu, acc[c][v], off);
-                if (g == 0) {
+                if (d0.y < 0 && (int64_t)(-d0.y - 1) >= a.n_slots) {   // a slot beyond the scratch
+                    if (lane == 0) atomicOr(a.status, kStatusSlotRange);
+                } else if (g == 0) {
                     float* dst = (d0.y == 0) ? a.Y + (int64_t)d0.x * a.ldy
                                              : a.partials + (int64_t)(-d0.y - 1) * a.k;
 #pragma unroll

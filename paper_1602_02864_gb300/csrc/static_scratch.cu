@@ -51,9 +51,12 @@ static cudaError_t static_scratch_address(float** out) {
 // available here, so the last segment task of a row finds its first slot
 // from the task list: every segment but the last has the same length, so the
 // number of earlier segments is (e0_last - row_start) / (e0_last - e0_prev).
+// A row whose slots would fall outside [0, max_slots) -- a task list that does
+// not belong to row_ptr -- is left unwritten and sets kStatusSlotRange.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 combine_from_tasks_kernel(const int4* __restrict__ tasks, int64_t n_tasks, const int64_t* __restrict__ row_ptr,
-                          const float* __restrict__ partials, float* __restrict__ Y, int64_t ldy, int32_t k) {
+                          const float* __restrict__ partials, int64_t max_slots, float* __restrict__ Y, int64_t ldy,
+                          int32_t k, int32_t* status) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + w;
     if (t >= n_tasks) return;
@@ -61,11 +64,16 @@ combine_from_tasks_kernel(const int4* __restrict__ tasks, int64_t n_tasks, const
     if (d.y >= 0) return;                               // not a segment
     const int4 dn = tasks[t + 1];
     if (dn.y < 0 && dn.x == d.x) return;                // not the row's last segment
-    const int4 dp = tasks[t - 1];                       // a split row has >= 2 segments
+    const int4 dp = t > 0 ? tasks[t - 1] : d;           // a split row has >= 2 segments
     const int64_t e0 = ((int64_t)(uint32_t)d.z) | ((int64_t)d.w << 32);
     const int64_t ep = ((int64_t)(uint32_t)dp.z) | ((int64_t)dp.w << 32);
-    const int64_t before = (e0 - row_ptr[d.x]) / (e0 - ep);
-    const int64_t last = -(int64_t)d.y - 1, first = last - before;
+    const int64_t last = -(int64_t)d.y - 1;
+    const int64_t before = (t > 0 && dp.y < 0 && dp.x == d.x && e0 > ep) ? (e0 - row_ptr[d.x]) / (e0 - ep) : -1;
+    const int64_t first = last - before;
+    if (before < 1 || first < 0 || last >= max_slots) {
+        if (lane == 0) atomicOr(status, kStatusSlotRange);
+        return;
+    }
     for (int c = lane; c < k; c += 32) {
         float acc = 0.f;
         for (int64_t q = first; q <= last; ++q) acc += __ldcg(partials + q * k + c);
@@ -128,22 +136,10 @@ extern "C" int spmm_apply_csr_static(int64_t n_rows, int64_t n_cols, int64_t nnz
         set_error(std::string("spmm_apply_csr_static: clear status: ") + cudaGetErrorString(e));
         return SPMM_ERR_CUDA;
     }
-    // widest vector that divides k and keeps every X load and Y store aligned
-    const int esize = xtype == SPMM_F32 ? 4 : 2;
-    const uintptr_t xa = (uintptr_t)X, ya = (uintptr_t)Y;
-    int vec = 16 / esize;
-    for (; vec > 1; vec >>= 1) {
-        const int yv = std::min(vec, 4);
-        if (k % vec == 0 && ldx % vec == 0 && xa % (uintptr_t)(vec * esize) == 0 && ldy % yv == 0 &&
-            ya % (uintptr_t)(yv * 4) == 0)
-            break;
-    }
-    const int nvec = k / vec;
-    const int ch = nvec > 32 ? 2 : 1;
-    const int per = (nvec + ch - 1) / ch;
-    int lg = 0;
-    while ((1 << lg) < per) ++lg;
-
+    // the same lane geometry as spmm_apply; short-row runs walk whole rows
+    // per lane group and nothing is compensated, so the sums of rows on
+    // several lanes may be added in another order than on a handle
+    const LaneGeometry gm = lane_geometry(X, ldx, k, xtype, Y, ldy);
     FwdArgs a;
     a.row_ptr = row_ptr;
     a.col_idx = col_idx;
@@ -151,18 +147,20 @@ extern "C" int spmm_apply_csr_static(int64_t n_rows, int64_t n_cols, int64_t nnz
     a.tasks = reinterpret_cast<const int4*>(tasks);
     a.n_tasks = n_tasks;
     a.partials = scratch;
+    a.n_slots = kStaticSlots;
     a.X = X;
     a.ldx = ldx;
     a.Y = Y;
     a.ldy = ldy;
     a.k = k;
-    a.lanes_log2 = lg;
-    a.nvec = nvec;
+    a.lanes_log2 = gm.lanes_log2;
+    a.nvec = gm.nvec;
     a.status = status;
-    a.wait_ns = 2000000000ull;
+    a.wait_ns = kWaitNs;
     a.x_evict_last = 1;
     a.compensated = 0;
     a.partials_comp = nullptr;
+    const int vec = gm.vec, ch = gm.ch;
     if (xtype == SPMM_F32) e = launch_rows_f32(a, vmode, vec, ch, s);
     else if (xtype == SPMM_BF16) e = launch_rows_bf16(a, vmode, vec, ch, s);
     else e = launch_rows_f16(a, vmode, vec, ch, s);
@@ -172,11 +170,38 @@ extern "C" int spmm_apply_csr_static(int64_t n_rows, int64_t n_cols, int64_t nnz
     }
     if (n_segments > 0) {
         const dim3 grid((unsigned)((n_tasks + kWarpsPerBlock - 1) / kWarpsPerBlock));
-        combine_from_tasks_kernel<<<grid, kWarpsPerBlock * 32, 0, s>>>(a.tasks, n_tasks, row_ptr, scratch, Y, ldy, k);
+        combine_from_tasks_kernel<<<grid, kWarpsPerBlock * 32, 0, s>>>(a.tasks, n_tasks, row_ptr, scratch,
+                                                                       kStaticSlots, Y, ldy, k, status);
         if ((e = cudaGetLastError()) != cudaSuccess) {
             set_error(std::string("spmm_apply_csr_static: combine kernel: ") + cudaGetErrorString(e));
             return SPMM_ERR_CUDA;
         }
+    }
+    return SPMM_OK;
+}
+
+extern "C" int spmm_static_status(void* stream) {
+    float* scratch = nullptr;
+    cudaError_t e = static_scratch_address(&scratch);
+    if (e != cudaSuccess) {
+        set_error(std::string("spmm_static_status: static scratch address: ") + cudaGetErrorString(e));
+        return SPMM_ERR_CUDA;
+    }
+    const int32_t* status = reinterpret_cast<const int32_t*>(scratch + kStaticSlots * kSlotStride);
+    int32_t st = 0;
+    if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess ||
+        (e = cudaMemcpy(&st, status, sizeof(st), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+        set_error(std::string("spmm_static_status: ") + cudaGetErrorString(e));
+        return SPMM_ERR_CUDA;
+    }
+    if (st & kStatusTimeout) {
+        set_error("spmm_static_status: a staging wait of the last call timed out; its Y is incomplete");
+        return SPMM_ERR_TIMEOUT;
+    }
+    if (st & kStatusSlotRange) {
+        set_error("spmm_static_status: the last call's task list named a partial slot beyond the static "
+                  "scratch (tasks not planned for this row_ptr?); its split rows are missing from Y");
+        return SPMM_ERR_FORMAT;
     }
     return SPMM_OK;
 }

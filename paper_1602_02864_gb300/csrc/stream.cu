@@ -192,6 +192,7 @@ int stream_apply(const spmm_mat* A, const void* X, int64_t ldx, int32_t k, int32
     int vec = 1, ch = 1;
     set_geometry(a, X, ldx, k, xtype, Y, ldy, d, &vec, &ch);
     a.partials = d.partials;
+    a.n_slots = d.n_slots;
     a.status = A->status;
     a.wait_ns = kWaitNs;
     a.x_evict_last = A->params.x_evict_last;

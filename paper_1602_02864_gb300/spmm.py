@@ -85,6 +85,8 @@ _lib.spmm_plan_walk_eff.restype = ctypes.c_int
 _lib.spmm_apply_csr_static.argtypes = [_i64, _i64, _i64, _P, _P, _P, ctypes.c_int, _P, _i64, _i64, _P, _i64,
                                        _i32, ctypes.c_int, _P, _i64, _P]
 _lib.spmm_apply_csr_static.restype = ctypes.c_int
+_lib.spmm_static_status.argtypes = [_P]
+_lib.spmm_static_status.restype = ctypes.c_int
 _lib.spmm_pagerank.argtypes = [_P, ctypes.c_double, _i32, _P, _P, _P, _P]
 _lib.spmm_pagerank.restype = ctypes.c_int
 _lib.spmm_create_batched.argtypes = [ctypes.POINTER(_P), _i32, _P, _P, _P, _P, _P, ctypes.c_int, _u32,
@@ -239,6 +241,12 @@ def spmm_apply_csr_static(n_rows, n_cols, nnz, row_ptr, col_idx, values, vtype, 
     _check(_lib.spmm_apply_csr_static(int(n_rows), int(n_cols), int(nnz), _ptr(row_ptr), _ptr(col_idx),
                                       _ptr(values), int(vtype), _ptr(tasks), int(n_tasks), int(n_segments), _ptr(X),
                                       int(ldx), int(k), int(xtype), _ptr(Y), int(ldy), _stream_handle(stream)))
+
+
+def spmm_static_status(stream=None):
+    """Raise SpmmError if the last spmm_apply_csr_static call on this device
+    timed out or named partial-sum slots beyond the static scratch."""
+    _check(_lib.spmm_static_status(_stream_handle(stream)))
 
 
 def spmm_pagerank(h, damping, iters, x, x0=None, stream=None) -> np.ndarray:

@@ -92,6 +92,20 @@ typedef enum {
  *              more lanes or its lanes hold at most 8 bytes, else whole
  *              rows.  Per orientation, like the plan.  Results differ
  *              between 1 and 2 only in the order of float32 additions.
+ *   hot_cols   create only: the H most-referenced columns of each
+ *              orientation (with >= 2 stored entries, most first) are
+ *              "hot".  A second copy of the column indices names them by
+ *              rank, and calls whose X rows take 4 bytes (k = 1 float32,
+ *              k = 2 bf16/f16 with 4-byte aligned rows) copy their X rows
+ *              into shared memory once per block and gather them from
+ *              there (Section 3.4's cache blocking of the dense rows a tile
+ *              reads).  Costs 4 bytes per stored entry plus 8 bytes per hot
+ *              column of device memory per orientation.  0: default =
+ *              automatic (H = 8192, for orientations with at least 2^20
+ *              entries whose kernel has room for 4096 or more beside its
+ *              staging buffers: pattern matrices); -1: none; > 0: at most
+ *              that many, capped by the room in shared memory.  Results are
+ *              the same sums in the same order as without.
  */
 typedef struct {
     int32_t task_nnz;
@@ -103,6 +117,7 @@ typedef struct {
     int32_t debug_fail_block;
     int32_t compensated;
     int32_t short_runs;
+    int32_t hot_cols;
 } spmm_opts;
 
 /* Plan statistics reported by spmm_get_info. */
@@ -130,6 +145,8 @@ typedef struct {
      * (or 0). */
     double walk_eff[4];
     double walk_eff_t[4];
+    int64_t n_hot;               /* hot columns of the forward orientation (spmm_opts.hot_cols) */
+    int64_t n_hot_t;             /* ... of the transposed orientation (or 0)        */
 } spmm_info;
 
 /*

@@ -53,6 +53,9 @@ static void free_dev(DevCSR& d) {
     cudaFree(d.partials_comp);
     cudaFree(d.perm);
     cudaFree(d.task_ctr);
+    cudaFree(d.col_hot);
+    cudaFree(d.hot_cols);
+    cudaFree(d.xh);
     d = DevCSR{};
 }
 
@@ -72,10 +75,13 @@ static cudaError_t upload(T** dst, const T* src, size_t count, size_t pad, cudaS
 
 // Copy one orientation (host CSR) and its plan to the device.
 // With `reorder`, the columns are relabelled by decreasing count of stored
-// entries (the device keeps the original index of each new label).
+// entries (the device keeps the original index of each new label).  Hot
+// columns (hot.cu): p.hot_cols -1 = automatic (kHotAuto), 0 = none, > 0 = at
+// most that many, never more than fit the hot variant's shared memory;
+// col_counts, if given, are the stored entries per column.
 static int build_orientation(DevCSR& d, int64_t n_rows, int64_t n_cols, const int64_t* row_ptr,
                              const int32_t* col_idx, const void* val, size_t vsize, const Params& p,
-                             bool reorder, cudaStream_t s, int64_t* bytes) {
+                             bool reorder, const int64_t* col_counts, cudaStream_t s, int64_t* bytes) {
     d.n_rows = n_rows;
     d.n_cols = n_cols;
     d.short_runs = p.short_runs;
@@ -85,22 +91,40 @@ static int build_orientation(DevCSR& d, int64_t n_rows, int64_t n_cols, const in
     cudaError_t e;
     if ((e = upload(&d.row_ptr, row_ptr, (size_t)n_rows + 1, 2, s, bytes)) != cudaSuccess)
         return cuda_fail(e, "row_ptr");
-    if (reorder) {
-        std::vector<int32_t> old_of_new, relabelled;
-        try {
+    const int64_t cap = hot_capacity(val ? 1 : 0);
+    const int64_t want_hot = p.hot_cols >= 0 ? std::min(p.hot_cols, cap)
+                             : (d.nnz >= kHotMinNnz && cap >= kHotAutoMin) ? std::min(kHotAuto, cap)
+                                                                           : 0;
+    std::vector<int32_t> old_of_new, relabelled, hot, encoded;
+    const int32_t* cols = col_idx;
+    try {
+        if (reorder) {
             relabel_by_degree(n_cols, col_idx, d.nnz, old_of_new, relabelled);
-        } catch (const std::bad_alloc&) {
-            set_error("create: out of host memory for the column relabelling");
-            return SPMM_ERR_OOM;
+            cols = relabelled.data();
+            col_counts = nullptr;   // counted again under the new labels
         }
-        if ((e = upload(&d.col_idx, relabelled.data(), (size_t)d.nnz, 8, s, bytes)) != cudaSuccess ||
-            (e = upload(&d.perm, old_of_new.data(), (size_t)n_cols, 0, s, bytes)) != cudaSuccess)
-            return cuda_fail(e, "col_idx");
-        // the host vectors are freed on return: finish their copies first
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "col_idx");
-    } else if ((e = upload(&d.col_idx, col_idx, (size_t)d.nnz, 8, s, bytes)) != cudaSuccess) {
-        return cuda_fail(e, "col_idx");
+        if (want_hot > 0) hot_select(n_cols, cols, d.nnz, col_counts, want_hot, hot, encoded);
+    } catch (const std::bad_alloc&) {
+        set_error("create: out of host memory for the column relabelling");
+        return SPMM_ERR_OOM;
     }
+    if (reorder && (e = upload(&d.perm, old_of_new.data(), (size_t)n_cols, 0, s, bytes)) != cudaSuccess)
+        return cuda_fail(e, "col_idx");
+    if ((e = upload(&d.col_idx, cols, (size_t)d.nnz, 8, s, bytes)) != cudaSuccess) return cuda_fail(e, "col_idx");
+    if (!hot.empty()) {
+        if ((e = upload(&d.col_hot, encoded.data(), (size_t)d.nnz, 8, s, bytes)) != cudaSuccess ||
+            (e = upload(&d.hot_cols, hot.data(), hot.size(), 0, s, bytes)) != cudaSuccess)
+            return cuda_fail(e, "hot columns");
+        const size_t xb = (hot.size() * kHotRowBytes + 15) & ~(size_t)15;
+        if ((e = cudaMalloc(&d.xh, xb)) != cudaSuccess) {
+            d.xh = nullptr;
+            return cuda_fail(e, "hot rows of X");
+        }
+        *bytes += (int64_t)xb;
+        d.n_hot = (int64_t)hot.size();
+    }
+    // the host vectors are freed on return: finish their copies first
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "col_idx");
     if (val) {
         if ((e = upload((char**)&d.val, (const char*)val, (size_t)d.nnz * vsize, 8 * vsize, s, bytes)) != cudaSuccess)
             return cuda_fail(e, "values");
@@ -150,6 +174,7 @@ static Params resolve_params(const spmm_opts* opts) {
         if (opts->debug_fail_block > 0) prm.fail_block = opts->debug_fail_block;
         prm.compensated = opts->compensated ? 1 : 0;
         prm.short_runs = (opts->short_runs == 1 || opts->short_runs == 2) ? opts->short_runs : 0;
+        if (opts->hot_cols != 0) prm.hot_cols = opts->hot_cols < 0 ? 0 : opts->hot_cols;
     }
     prm.task_nnz = std::min(std::max(prm.task_nnz, 32), kMaxTaskNnz);
     prm.task_rows = std::min(std::max(prm.task_rows, 1), kMaxTaskRows);
@@ -343,7 +368,7 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
         *out = A;
         return SPMM_OK;
     }
-    rc = build_orientation(A->fwd, n_rows, n_cols, row_ptr, col_idx, values, vsize, prm, reorder, s,
+    rc = build_orientation(A->fwd, n_rows, n_cols, row_ptr, col_idx, values, vsize, prm, reorder, nullptr, s,
                            &A->device_bytes);
     if (rc == SPMM_OK && (flags & SPMM_WANT_TRANSPOSE)) {
         // CSR of A^T by a stable counting sort on the column index.
@@ -367,8 +392,11 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
                     tidx[(size_t)q] = (int32_t)i;
                     if (values) std::memcpy(&tval[(size_t)q * vsize], (const char*)values + p * vsize, vsize);
                 }
+            // the columns of A^T are the rows of A: their entry counts are A's row lengths
+            std::vector<int64_t> outdeg((size_t)n_rows);
+            for (int64_t i = 0; i < n_rows; ++i) outdeg[(size_t)i] = row_ptr[i + 1] - row_ptr[i];
             rc = build_orientation(A->tr, n_cols, n_rows, tptr.data(), tidx.data(), values ? tval.data() : nullptr,
-                                   vsize, prm, reorder, s, &A->device_bytes);
+                                   vsize, prm, reorder, outdeg.data(), s, &A->device_bytes);
             A->has_tr = (rc == SPMM_OK);
         }
     }
@@ -648,11 +676,21 @@ int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int3
     FwdArgs a;
     int vec = 1, ch = 1;
     set_geometry(a, X, ldx, k, xtype, Y, ldy, d, &vec, &ch);
+    const int esize = (int)dtype_size(xtype);
+    a.col_idx = d.col_idx;
+    if (d.n_hot > 0 && k * esize == kHotRowBytes && ch == 1 && a.lanes_log2 == 0) {
+        // one lane per 4-byte X row: the hot variant, fed with the packed hot
+        // rows of X and the column indices that name them
+        const cudaError_t eh = hot_gather(d, X, ldx, k, esize, s);
+        if (eh != cudaSuccess) return cuda_fail(eh, "spmm_apply: hot rows");
+        a.col_idx = d.col_hot;
+        a.Xh = d.xh;
+        a.hot_bytes = (d.n_hot * k * esize + 15) & ~(int64_t)15;
+    }
     cudaError_t ec = cudaSuccess;
     a.task_ctr = task_counter(d, k, xtype, s, &ec, &a.task_chunk);
     if (ec != cudaSuccess) return cuda_fail(ec, "spmm_apply: task counter");
     a.row_ptr = d.row_ptr;
-    a.col_idx = d.col_idx;
     a.val = d.val;
     a.tasks = d.tasks;
     a.n_tasks = d.n_tasks;
@@ -710,6 +748,8 @@ extern "C" int spmm_get_info(spmm_mat_t A, spmm_info* info) {
     info->value_dtype = A->vtype;
     info->has_transpose = A->has_tr ? 1 : 0;
     info->n_graphs = (int32_t)(A->row_off.size() - 1);
+    info->n_hot = A->fwd.n_hot;
+    info->n_hot_t = A->has_tr ? A->tr.n_hot : 0;
     for (int i = 0; i < 4; ++i) {
         info->walk_eff[i] = A->fwd.walk_eff[i];
         info->walk_eff_t[i] = A->has_tr ? A->tr.walk_eff[i] : 0.0;
@@ -844,7 +884,9 @@ extern "C" int spmm_replan(spmm_mat_t A, const spmm_opts* opts, int32_t transpos
         // the L2 policy and compensation are launch parameters shared by both orientations
         A->params.x_evict_last = p.x_evict_last;
         A->params.compensated = p.compensated;
+        const int64_t hot_cols = A->params.hot_cols;   // fixed at create (the stored column indices)
         if (!transpose) A->params = p;
+        A->params.hot_cols = hot_cols;
     }
     return rc;
 }

@@ -64,6 +64,15 @@ struct DevCSR {
     int32_t* perm = nullptr;        // SPMM_REORDER: original index of relabelled column c (n_cols)
     unsigned long long* task_ctr = nullptr;   // task counter of dynamically scheduled launches
     int32_t short_runs = 0;         // short-row runs over lane groups (spmm_opts.short_runs)
+    // hot columns (hot.cu): col_hot is col_idx with ~slot for an entry in one
+    // of the n_hot most-referenced columns, hot_cols[slot] that column; calls
+    // with X rows of at most 4 bytes copy the hot rows of X into xh (packed,
+    // kHotRowBytes each) and run the kernel variant that keeps them in
+    // shared memory
+    int32_t* col_hot = nullptr;     // padded by 8 entries, like col_idx
+    int32_t* hot_cols = nullptr;
+    int64_t n_hot = 0;
+    void* xh = nullptr;
     double walk_eff[4] = {1.0, 1.0, 1.0, 1.0};   // HostPlan::walk_eff of the current plan
 };
 
@@ -118,6 +127,7 @@ struct Params {
     int32_t fail_block = 0;
     int32_t compensated = 0;            // compensated sums for long rows and hub segments
     int32_t short_runs = 0;             // 0 automatic, 1 row walk, 2 pieces per lane group
+    int64_t hot_cols = -1;              // hot columns per orientation: -1 automatic, 0 none (create only)
 };
 
 }  // namespace spmm
@@ -174,6 +184,34 @@ void relabel_by_degree(int64_t n_cols, const int32_t* col_idx, int64_t nnz, std:
 int reorder_reserve(spmm_mat* A, int64_t n_in, int32_t k, int32_t xtype, cudaStream_t s);
 int reorder_x(spmm_mat* A, const DevCSR& d, const void* X, int64_t ldx, int32_t k, int32_t xtype, cudaStream_t s,
               const void** Xp);
+
+// hot.cu: rank the columns by stored entries (counts, or counted from
+// col_idx when counts is null), keep the max_hot most-referenced ones that
+// have at least two entries (hot_cols: slot -> column, most referenced
+// first) and write col_idx with hot entries as ~slot to `encoded`; returns H
+int64_t hot_select(int64_t n_cols, const int32_t* col_idx, int64_t nnz, const int64_t* counts, int64_t max_hot,
+                   std::vector<int32_t>& hot_cols, std::vector<int32_t>& encoded);
+// enqueue Xh[s, :] = X[hot_cols[s], :] (k elements of esize bytes) for the
+// n_hot hot columns of d
+cudaError_t hot_gather(const DevCSR& d, const void* X, int64_t ldx, int32_t k, int esize, cudaStream_t s);
+// hot rows that fit the shared memory of the hot kernel variant beside its
+// warps' staging buffers (value mode vmode, at most 4-byte rows); 0 if none
+int64_t hot_capacity(int vmode);
+// The hot variant runs one block of kHotWarps warps per SM (the warps of
+// three blocks of the plain kernel) for calls whose X rows take exactly
+// kHotRowBytes bytes.  Automatic hot columns: kHotAuto of them (32 KB of
+// shared memory) for orientations of at least kHotMinNnz entries, when at
+// least kHotAutoMin fit.  On R-MAT scale 24 (k = 1 float32, one block of 24
+// warps) 4096 / 8192 / 16384 / 24576 hot rows took 0.859 / 0.828 / 0.845 /
+// 1.320 ms against 0.923 ms without: every 32 KB taken from L1 costs L1 hits
+// of the other gathers, and at 24576 L1 is almost gone.  With 16 warps the
+// same sizes were slower than without; rows of 2 bytes (bf16 k = 1) were
+// slower with any hot rows (1.04 against 0.87 ms), so they do not use them.
+constexpr int kHotWarps = 24;
+constexpr int kHotRowBytes = 4;
+constexpr int64_t kHotAuto = 8192;
+constexpr int64_t kHotAutoMin = 4096;
+constexpr int64_t kHotMinNnz = 1 << 20;
 
 // abi.cu
 void set_error(const std::string& msg);
@@ -238,6 +276,11 @@ struct FwdArgs {
     // short-row runs over rows of several lanes: 1 = merge-based pieces per
     // lane group, 0 = each group walks whole rows
     int32_t merge_groups = 0;
+    // hot variant: a negative column index c names row ~c of the hot rows,
+    // hot_bytes (a multiple of 16) of them packed at Xh, copied into shared
+    // memory at the start of each block
+    const void* Xh = nullptr;
+    int64_t hot_bytes = 0;
 };
 
 // Launches from a handle are scheduled dynamically.  Tasks over wide X rows
@@ -268,6 +311,11 @@ cudaError_t launch_rows_f16_one(const FwdArgs& a, int vmode, int vec, int ch, cu
 cudaError_t launch_rows_f32_mg(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
 cudaError_t launch_rows_bf16_mg(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
 cudaError_t launch_rows_f16_mg(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s);
+// one lane per X row of at most 4 bytes with the hot rows in shared memory
+// (FwdArgs::Xh set)
+cudaError_t launch_rows_f32_hot(const FwdArgs& a, int vmode, int vec, cudaStream_t s);
+cudaError_t launch_rows_bf16_hot(const FwdArgs& a, int vmode, int vec, cudaStream_t s);
+cudaError_t launch_rows_f16_hot(const FwdArgs& a, int vmode, int vec, cudaStream_t s);
 
 // combine.cu: Y[row] = sum of the split row's partials in a fixed order.
 cudaError_t launch_combine(const int4* splits, int64_t n_splits, const float* partials, float* Y,

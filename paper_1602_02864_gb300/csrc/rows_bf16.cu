@@ -5,6 +5,7 @@
 namespace spmm {
 
 cudaError_t launch_rows_bf16(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
+    if (a.Xh && ch == 1 && a.lanes_log2 == 0) return launch_rows_bf16_hot(a, vmode, vec, s);
     if (ch == 1 && a.lanes_log2 == 0) return launch_rows_bf16_one(a, vmode, vec, ch, s);
     if (a.merge_groups) return launch_rows_bf16_mg(a, vmode, vec, ch, s);
     return launch_rows_t<__nv_bfloat16, false>(a, vmode, vec, ch, s);

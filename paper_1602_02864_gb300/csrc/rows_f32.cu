@@ -5,6 +5,7 @@
 namespace spmm {
 
 cudaError_t launch_rows_f32(const FwdArgs& a, int vmode, int vec, int ch, cudaStream_t s) {
+    if (a.Xh && ch == 1 && a.lanes_log2 == 0) return launch_rows_f32_hot(a, vmode, vec, s);
     if (ch == 1 && a.lanes_log2 == 0) return launch_rows_f32_one(a, vmode, vec, ch, s);
     if (a.merge_groups) return launch_rows_f32_mg(a, vmode, vec, ch, s);
     return launch_rows_t<float, false>(a, vmode, vec, ch, s);

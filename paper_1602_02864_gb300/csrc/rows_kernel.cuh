@@ -184,6 +184,12 @@ struct XVec {
     __device__ __forceinline__ float get(int i) const {
         return bits_to_f32<XT>((i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xffffu));
     }
+    // the same elements from shared memory (VEC <= 2: rows of at most 4 bytes)
+    __device__ __forceinline__ void load_sh(const XT* p) {
+        static_assert(VEC <= 2, "shared-memory rows of at most 4 bytes");
+        if constexpr (VEC == 2) w[0] = *reinterpret_cast<const uint32_t*>(p);
+        else w[0] = *reinterpret_cast<const unsigned short*>(p);
+    }
 };
 
 template <int VEC>
@@ -201,6 +207,10 @@ struct XVec<float, VEC> {
         }
     }
     __device__ __forceinline__ float get(int i) const { return f[i]; }
+    __device__ __forceinline__ void load_sh(const float* p) {
+        static_assert(VEC == 1, "shared-memory rows of at most 4 bytes");
+        f[0] = *p;
+    }
 };
 
 // Store VEC floats to an address aligned to min(VEC, 4) * 4 bytes.
@@ -314,10 +324,24 @@ constexpr int min_blocks() {
 // row (CH == 1) and short-row runs merge-based over lane groups, with 3
 // blocks per SM and 4 nonzeros in flight per group (MG == 1) or 4 blocks and
 // 2 in flight (MG == 2).
-template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, int MG = 0>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())) rows_kernel(FwdArgs a) {
+// Warps per block: kWarpsPerBlock, or kHotWarps in one block per SM for the
+// instantiations that keep the hot rows of X in shared memory (HOT).
+template <bool HOT>
+constexpr int warps_per_block() {
+    return HOT ? kHotWarps : kWarpsPerBlock;
+}
+
+// HOT: one lane per X row of at most 4 bytes; a negative column index c
+// names row ~c of the hot rows of X, which the block copies into shared
+// memory (after its warps' staging buffers) before its first task, so those
+// gathers leave the L1-to-L2 request path alone (hot.cu).
+template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, int MG = 0, bool HOT = false>
+__global__ void __launch_bounds__(warps_per_block<HOT>() * 32, (HOT ? 1 : min_blocks<VMODE, MG>()))
+    rows_kernel(FwdArgs a) {
     static_assert(!ONE || CH == 1, "one lane per row needs CH == 1");
     static_assert(MG == 0 || (!ONE && CH == 1), "merge over lane groups needs several lanes and CH == 1");
+    static_assert(!HOT || (ONE && MG == 0 && VEC * sizeof(XT) <= 4), "hot rows in shared memory: <= 4-byte rows");
+    constexpr int WPB = warps_per_block<HOT>();
     constexpr bool kFlat = ONE && VEC == 1 && SPMM_K1_FLAT;
     // merge-based runs pay off for X rows of up to 8 bytes; for 16-byte rows
     // (mostly gathered from DRAM) the row-per-lane walk measured faster
@@ -344,9 +368,30 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* wb = smem + w * Lay::kWarp;
     uint64_t* bars = reinterpret_cast<uint64_t*>(wb + 2 * Lay::kBuf);
+    const XT* hs = nullptr;     // hot rows of X in shared memory (HOT)
+    if constexpr (HOT) {
+        // one bulk copy of the packed hot rows, before any warp leaves
+        uint64_t* hbar = reinterpret_cast<uint64_t*>(smem + WPB * Lay::kWarp);
+        hs = reinterpret_cast<const XT*>(smem + WPB * Lay::kWarp + 16);
+        if (threadIdx.x == 0) {
+            mbar_init(hbar, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect_tx(hbar, (uint32_t)a.hot_bytes);
+            bulk_g2s(const_cast<XT*>(hs), a.Xh, (uint32_t)a.hot_bytes, hbar, policy_evict_last());
+        }
+        if (!mbar_wait_bounded(hbar, 0, a.wait_ns)) {
+            if (threadIdx.x == 0) atomicOr(a.status, kStatusTimeout);
+            // the copy may still be in flight: wait for it (bounded) before leaving
+            mbar_wait_bounded(hbar, 0, a.wait_ns);
+            return;
+        }
+    }
 
-    const int64_t W = (int64_t)gridDim.x * kWarpsPerBlock;
-    int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+    const int64_t W = (int64_t)gridDim.x * WPB;
+    int64_t t = (int64_t)blockIdx.x * WPB + w;
     if (t >= a.n_tasks) return;
     if (lane == 0) {
         mbar_init(&bars[0], 1);
@@ -366,6 +411,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
 
     const uint64_t apol = policy_evict_first();
     const uint64_t xpol = a.x_evict_last ? policy_evict_last() : policy_evict_normal();
+    // load the X row of column index c (elements off.. of this lane's part)
+    auto gather = [&](auto& xv, int64_t c, int off) {
+        if constexpr (HOT) {
+            if (c < 0) {
+                xv.load_sh(hs + (int64_t)(~c) * VEC);
+                return;
+            }
+        }
+        xv.load(xb + c * a.ldx + off, xpol);
+    };
     int4 d0 = a.tasks[t], d1 = a.tasks[t + 1];
     if (lane == 0) issue_task<VMODE>(a, d0, d1, wb, &bars[0], apol);
     // the next task: static stride, or the next of a chunk claimed from the
@@ -439,7 +494,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
                             const int64_t cidx = st.col[idx];
                             av[u] = staged_val<VMODE>(st.val, idx);
                             XVec<XT, 1> t1;
-                            t1.load(xb + cidx * a.ldx, xpol);
+                            gather(t1, cidx, 0);
                             xv[u] = t1.get(0);
                         }
                     }
@@ -512,7 +567,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
                             if (i + u < ce) {
                                 const int64_t cidx = st.col[i + u];
                                 av[u] = staged_val<VMODE>(st.val, i + u);
-                                xv[u].load(xb + cidx * a.ldx, xpol);
+                                gather(xv[u], cidx, 0);
                             }
 #pragma unroll
                         for (int u = 0; u < UM; ++u)
@@ -611,7 +666,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
                             if (i + u < ce) {
                                 const int64_t cidx = st.col[i + u];
                                 av[u] = staged_val<VMODE>(st.val, i + u);
-                                if (act[0]) xv[u].load(xb + cidx * a.ldx, xpol);
+                                if (act[0]) gather(xv[u], cidx, 0);
                             }
 #pragma unroll
                         for (int u = 0; u < UW; ++u)
@@ -682,7 +737,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
                                 av[u] = staged_val<VMODE>(st.val, i + u);
 #pragma unroll
                                 for (int c = 0; c < CH; ++c)
-                                    if (act[c]) xv[u][c].load(xb + cidx * a.ldx + c * LANES * VEC, xpol);
+                                    if (act[c]) gather(xv[u][c], cidx, c * LANES * VEC);
                             }
                         }
 #pragma unroll
@@ -718,7 +773,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
                             av[u] = staged_val<VMODE>(st.val, idx);
 #pragma unroll
                             for (int c = 0; c < CH; ++c)
-                                if (act[c]) xv[u][c].load(xb + cidx * a.ldx + c * LANES * VEC, xpol);
+                                if (act[c]) gather(xv[u][c], cidx, c * LANES * VEC);
                         }
                     }
 #pragma unroll
@@ -792,7 +847,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
                             av[u] = staged_val<VMODE>(st.val, idx);
 #pragma unroll
                             for (int c = 0; c < CH; ++c)
-                                if (act[c]) xv[u][c].load(xb + cidx * a.ldx + c * LANES * VEC, xpol);
+                                if (act[c]) gather(xv[u][c], cidx, c * LANES * VEC);
                         }
                     }
 #pragma unroll
@@ -828,35 +883,65 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, (min_blocks<VMODE, MG>())
     }
 }
 
-template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, int MG = 0>
+template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, int MG = 0, bool HOT = false>
 cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     using Lay = Layout<VMODE>;
+    constexpr int WPB = warps_per_block<HOT>();
+    constexpr int kStage = WPB * Lay::kWarp;      // staging buffers of the block's warps
     // per instantiation, computed once (thread-safe; a failure is reported to
     // every caller)
     static std::once_flag once;
-    static int blocks_per_sm = 0, num_sms = 0;
+    static int blocks_per_sm = 0, num_sms = 0, max_smem = 0;
     static cudaError_t setup = cudaSuccess;
     std::call_once(once, [] {
         cudaError_t e = cudaSuccess;
-        if (Lay::kBlock > 48 * 1024)
-            e = cudaFuncSetAttribute(rows_kernel<XT, VMODE, VEC, CH, COMP, ONE, MG>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::kBlock);
-        int dev = 0, nb = 0, sms = 0;
+        int dev = 0, nb = 0, sms = 0, opt = 0;
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&opt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        // the hot variant asks for the whole opt-in shared memory (its hot rows fill what the staging leaves)
+        const int want = HOT ? opt : kStage;
+        if (e == cudaSuccess && want > 48 * 1024)
+            e = cudaFuncSetAttribute(rows_kernel<XT, VMODE, VEC, CH, COMP, ONE, MG, HOT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, want);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rows_kernel<XT, VMODE, VEC, CH, COMP, ONE, MG>,
-                                                              kWarpsPerBlock * 32, Lay::kBlock);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rows_kernel<XT, VMODE, VEC, CH, COMP, ONE, MG, HOT>,
+                                                              WPB * 32, want);
         setup = e;
         num_sms = sms;
+        max_smem = opt;
         blocks_per_sm = nb > 0 ? nb : 1;
     });
     if (setup != cudaSuccess) return setup;
-    const int64_t want = (a.n_tasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    size_t smem = kStage;
+    if constexpr (HOT) {
+        smem += 16 + (size_t)a.hot_bytes;
+        if (smem > (size_t)max_smem || a.hot_bytes <= 0 || a.hot_bytes % 16) return cudaErrorInvalidValue;
+    }
+    const int64_t want = (a.n_tasks + WPB - 1) / WPB;
     const int64_t cap = (int64_t)blocks_per_sm * num_sms;
     const dim3 grid((unsigned)(want < cap ? want : cap));
-    rows_kernel<XT, VMODE, VEC, CH, COMP, ONE, MG><<<grid, kWarpsPerBlock * 32, Lay::kBlock, s>>>(a);
+    rows_kernel<XT, VMODE, VEC, CH, COMP, ONE, MG, HOT><<<grid, WPB * 32, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// One lane per X row of at most 4 bytes, hot rows in shared memory.
+template <typename XT>
+cudaError_t launch_rows_hot_t(const FwdArgs& a, int vmode, int vec, cudaStream_t s) {
+    if (a.n_tasks <= 0) return cudaSuccess;
+#define SPMM_LAUNCH_HOT(VM, V)                                                           \
+    if (vmode == VM && vec == V)                                                         \
+        return a.compensated ? launch_one<XT, VM, V, 1, true, true, 0, true>(a, s)       \
+                             : launch_one<XT, VM, V, 1, false, true, 0, true>(a, s);
+    if constexpr (sizeof(XT) == 4) {
+        SPMM_LAUNCH_HOT(0, 1) SPMM_LAUNCH_HOT(1, 1)
+    } else {
+        constexpr int VM3 = std::is_same<XT, __half>::value ? 3 : 2;
+        SPMM_LAUNCH_HOT(0, 1) SPMM_LAUNCH_HOT(0, 2) SPMM_LAUNCH_HOT(1, 1) SPMM_LAUNCH_HOT(1, 2)
+        SPMM_LAUNCH_HOT(VM3, 1) SPMM_LAUNCH_HOT(VM3, 2)
+    }
+#undef SPMM_LAUNCH_HOT
+    return cudaErrorInvalidValue;
 }
 
 template <typename XT, bool ONE, int MG = 0>

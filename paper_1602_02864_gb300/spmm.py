@@ -41,7 +41,7 @@ class spmm_opts(ctypes.Structure):
     _fields_ = [("task_nnz", ctypes.c_int32), ("task_rows", ctypes.c_int32), ("long_row", ctypes.c_int32),
                 ("short_max", ctypes.c_int32), ("x_l2_policy", ctypes.c_int32), ("stream_slot_kib", ctypes.c_int32),
                 ("debug_fail_block", ctypes.c_int32), ("compensated", ctypes.c_int32),
-                ("short_runs", ctypes.c_int32)]
+                ("short_runs", ctypes.c_int32), ("hot_cols", ctypes.c_int32)]
 
 
 class spmm_tile_desc(ctypes.Structure):
@@ -53,7 +53,8 @@ class spmm_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("n_rows", "n_cols", "nnz", "n_tasks", "n_split_rows", "n_segments",
                                               "n_tasks_t", "n_split_rows_t", "n_segments_t", "device_bytes")] + [
         ("value_dtype", ctypes.c_int32), ("has_transpose", ctypes.c_int32), ("n_graphs", ctypes.c_int32),
-        ("reserved", ctypes.c_int32), ("walk_eff", ctypes.c_double * 4), ("walk_eff_t", ctypes.c_double * 4)]
+        ("reserved", ctypes.c_int32), ("walk_eff", ctypes.c_double * 4), ("walk_eff_t", ctypes.c_double * 4),
+        ("n_hot", ctypes.c_int64), ("n_hot_t", ctypes.c_int64)]
 
 
 if not os.path.exists(LIB_PATH):

@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--reorder", action="store_true",
                     help="create the handle with SPMM_REORDER (columns relabelled by degree)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--transpose", action="store_true",
+                    help="the k sweep multiplies by A^T (the PageRank product is A^T at k = 1)")
+    ap.add_argument("--record-traffic", default=None, metavar="CSV",
+                    help="write the traffic record from an ncu raw CSV export of one rows_kernel launch, then exit")
     ap.add_argument("--pagerank-iters", type=int, default=30)
     ap.add_argument("--workload", default="ksweep",
                     choices=["ksweep", "streaming", "nmf-batched", "eigs", "gather-ceiling", "vpart", "ordering",
@@ -69,11 +73,71 @@ def metric_name(args):
     return f"SpMM nonzeros/s (R-MAT scale {args.scale}, k sweep {args.ks}{pr}, FP32 X)"
 
 
-# DRAM bytes of one PageRank iteration (product on A^T + combine + update +
-# reduce) measured with ncu on the default workload (R-MAT scale 24, edge
-# factor 16); see profiles/pagerank_iteration_rmat24.md.  Only reported for
-# that workload.
-PAGERANK_ITER_TRAFFIC = {(24, 16): 1.689e9}
+# DRAM traffic of the dominant kernel comes from a record that `--record-traffic`
+# writes from an ncu capture; the record holds a digest of the library's
+# sources and is used only while the sources are unchanged.
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "traffic_rows_kernel_k1.json")
+
+
+def source_digest() -> str:
+    """SHA-256 over the CUDA/C++ sources and the public header (file names
+    and contents, in name order)."""
+    import hashlib
+    h = hashlib.sha256()
+    dirs = [os.path.join(ROOT, "paper_1602_02864_gb300", "csrc"), os.path.join(ROOT, "include")]
+    for d in dirs:
+        for fn in sorted(os.listdir(d)):
+            if fn.endswith((".cu", ".cuh", ".h", ".cpp")):
+                h.update(fn.encode())
+                with open(os.path.join(d, fn), "rb") as f:
+                    h.update(f.read())
+    return h.hexdigest()
+
+
+def read_traffic(scale, edge_factor, nnz):
+    """DRAM bytes per launch of the k = 1 product (A X, float32) on this
+    workload, from the record if it matches the current sources, scaled by
+    stored entries when it was taken on a smaller graph; else None."""
+    try:
+        with open(TRAFFIC_RECORD) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None, "no record"
+    if rec.get("source_digest") != source_digest():
+        return None, "record taken on other sources"
+    if rec.get("edge_factor") != edge_factor or rec.get("transpose"):
+        return None, "record taken on another workload"
+    return rec["dram_bytes_per_launch"] * nnz / rec["nnz"], f"{TRAFFIC_RECORD[len(ROOT) + 1:]} (R-MAT scale " \
+        f"{rec['scale']}, scaled by stored entries)"
+
+
+def record_traffic(csv_path, args):
+    """Write the traffic record from an ncu --csv --page raw export of one
+    launch of rows_kernel (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    import csv
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(f)]
+    hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    names, units, data = rows[hdr], rows[hdr + 1], rows[hdr + 2:]
+    scale_of = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+    launches = [r for r in data if "rows_kernel" in r[names.index("Kernel Name")]]
+    if not launches:
+        raise SystemExit("record_traffic: no rows_kernel launch in " + csv_path)
+    r = launches[0]
+    tot = 0.0
+    for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        i = names.index(m)
+        tot += float(r[i].replace(",", "")) * scale_of[units[i]]
+    A, _ = make_graph(args)
+    rec = {"kernel": r[names.index("Kernel Name")], "scale": args.scale, "edge_factor": args.edge_factor,
+           "nnz": A.nnz, "dram_bytes_per_launch": tot, "source_digest": source_digest(),
+           "workload": f"R-MAT scale {args.scale}, {'A^T' if args.transpose else 'A'} X with k = 1 float32",
+           "transpose": bool(args.transpose)}
+    os.makedirs(os.path.dirname(TRAFFIC_RECORD), exist_ok=True)
+    with open(TRAFFIC_RECORD, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    print(json.dumps(rec))
 
 
 def pagerank_iter_bytes(nnz, n):
@@ -679,11 +743,11 @@ def workload_eigs(args):
 def workload_gather_ceiling(args):
     """Random-row gather ceilings: row sizes 4..256 B from tables inside L2
     (64 MB) and in DRAM (8 GB)."""
-    from paper_1602_02864_gb300 import spmm
+    from paper_1602_02864_gb300 import probe, spmm  # noqa: F401
     out = {}
     for rb in (4, 8, 16, 32, 64, 128, 256):
         for tb, name in (((64 << 20), "l2_64MB"), ((8 << 30), "dram_8GB")):
-            r, b = spmm.spmm_probe_gather(tb, rb)
+            r, b = probe.spmm_probe_gather(tb, rb)
             out[f"{rb}B_{name}"] = {"rows_per_s": r, "GBps": b / 1e9}
     best = max(v["rows_per_s"] for v in out.values())
     return base_line(args, "random row-gather ceiling (rows/s)", best, "rows/s", 0.0, "gather-ceiling", "f32",
@@ -695,6 +759,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.record_traffic:
+        return record_traffic(args.record_traffic, args)
     if args.impl == "reference":
         return reference_arm(args, rank, world)
     if args.workload != "ksweep":
@@ -708,7 +774,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_1602_02864_gb300 import spmm
+    from paper_1602_02864_gb300 import probe, spmm
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -724,7 +790,7 @@ def main():
     A, t_gen = make_graph(args)
     N, nnz = A.n_rows, A.nnz
     t0 = time.time()
-    h = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, transpose=args.pagerank_iters > 0,
+    h = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, transpose=args.pagerank_iters > 0 or args.transpose,
                           reorder=args.reorder)
     torch.cuda.synchronize()
     t_create = time.time() - t0
@@ -734,9 +800,9 @@ def main():
     cands = POWER_LAW_CANDIDATES
     tuned = {}
     kt = 8 if 8 in ks else ks[0]
-    best, times, _ = spmm.spmm_autotune(h.handle, kt, spmm.SPMM_F32, 0, cands, reps=2)
-    tuned["forward"] = dict(cands[best], k=kt, ms=round(float(times[best]), 4))
-    if args.pagerank_iters:
+    best, times, _ = spmm.spmm_autotune(h.handle, kt, spmm.SPMM_F32, int(args.transpose), cands, reps=2)
+    tuned["transpose" if args.transpose else "forward"] = dict(cands[best], k=kt, ms=round(float(times[best]), 4))
+    if args.pagerank_iters and not args.transpose:
         best, times, _ = spmm.spmm_autotune(h.handle, 1, spmm.SPMM_F32, 1, cands, reps=2)
         tuned["transpose"] = dict(cands[best], k=1, ms=round(float(times[best]), 4))
     t_tune = time.time() - t0
@@ -759,7 +825,7 @@ def main():
         for i, k in enumerate(ks):
             if ev is not None:
                 ev[i][0].record(stream)
-            h.apply(xs[k], Y=Y[k])
+            h.apply(xs[k], Y=Y[k], transpose=args.transpose)
             if ev is not None:
                 ev[i][1].record(stream)
         if args.pagerank_iters:
@@ -806,9 +872,6 @@ def main():
         B = alg_bytes(nnz, N, N, k, 4)
         breakdown[str(k)] = {"ms": round(ms, 4), "nnz_per_s": nnz / (ms / 1e3), "alg_GBps": B / (ms / 1e3) / 1e9,
                              "roofline_frac": B / (ms / 1e3) / 1e9 / peak_gbs}
-    kdom = max(ks, key=lambda k: statistics.median(per_k[k]))
-    dom = breakdown[str(kdom)]
-    dom_name = f"rows_kernel k={kdom} f32"
     pagerank = None
     if args.pagerank_iters:
         ms = statistics.median(pr_ms)
@@ -819,11 +882,19 @@ def main():
                     "nnz_per_s": nnz / (it_ms / 1e3), "alg_GBps": B / (it_ms / 1e3) / 1e9,
                     "roofline_frac": B / (it_ms / 1e3) / 1e9 / peak_gbs, "sum_x": float(xh.sum()),
                     "min_x": float(xh.min()), "residual_first_last": [float(pr_res[0][0]), float(pr_res[0][-1])]}
-        pagerank["traffic"] = PAGERANK_ITER_TRAFFIC.get((args.scale, args.edge_factor))
-        if ms > statistics.median(per_k[kdom]):
-            dom = pagerank
-            dom_name = ("PageRank iteration: rows_kernel on A^T (k=1, f32) + update + reduce; "
-                        f"{args.pagerank_iters} per CUDA-graph launch, timed per call")
+    # The dominant kernel: the task kernel's k = 1 instantiation (the k = 1
+    # product of the sweep and the A^T product of every PageRank iteration,
+    # 1 + iters launches per step), timed by the events around the sweep's
+    # k = 1 call (which also holds the hot-row copy and the split-row combine);
+    # otherwise the slowest k of the sweep.
+    kdom = 1 if (1 in ks and args.pagerank_iters) else max(ks, key=lambda k: statistics.median(per_k[k]))
+    dom = breakdown[str(kdom)]
+    launches = 1 + (args.pagerank_iters if kdom == 1 and not args.transpose else 0)
+    dom_name = (f"rows_kernel k={kdom} f32 ({'A^T' if args.transpose else 'A'} X; {launches} launches per step"
+                + (", the A^T product of each PageRank iteration included)" if launches > 1 else ")"))
+    traffic, traffic_src = (None, "not recorded for this k")
+    if kdom == 1 and not args.transpose:
+        traffic, traffic_src = read_traffic(args.scale, args.edge_factor, nnz)
 
     # ---- measured gather ceilings for each k (the dominant cost: one X row
     # per nonzero): uniformly random rows from a table of X's size, and this
@@ -833,14 +904,14 @@ def main():
         rb = 4
         while rb < 4 * k:
             rb *= 2
-        uni, _ = spmm.spmm_probe_gather(N * k * 4, rb)
-        own, _ = spmm.spmm_probe_gather_cols(h.handle, 0, 4 * k)
+        uni, _ = probe.spmm_probe_gather(N * k * 4, rb)
+        own, _ = probe.spmm_probe_gather_cols(h.handle, 0, 4 * k)
         ceilings[str(k)] = {"table_MB": round(N * k * 4 / 1e6, 1), "uniform_rows_per_s": uni,
                             "matrix_stream_rows_per_s": own,
                             "frac_of_matrix_stream": breakdown[str(k)]["nnz_per_s"] / own}
     pr_ceiling = None
     if args.pagerank_iters and not args.no_ceiling:
-        own, _ = spmm.spmm_probe_gather_cols(h.handle, 1, 4)
+        own, _ = probe.spmm_probe_gather_cols(h.handle, 1, 4)
         pr_ceiling = {"matrix_stream_rows_per_s": own, "frac_of_matrix_stream": pagerank["nnz_per_s"] / own}
 
     # ---- BF16 X: speedup over FP32 and error on sampled rows vs the oracle
@@ -886,73 +957,45 @@ def main():
         got = Y[k].index_select(0, sample_t).cpu().numpy().astype(np.float64)
         parity[str(k)] = float((np.abs(got - ref) / np.maximum(scale[k], 1e-300)).max())
 
-    # ---- end to end: pinned host X -> device, apply, Y -> pinned host, through
-    # the public API on three streams (copy in, compute, copy out) so the copies
-    # of one k overlap the product of another and both link directions run at once
+    # ---- end to end through the library's host-buffer entry point: every
+    # step hands the sweep's X matrices (pinned host memory, one contiguous
+    # row-major part per k) to spmm_apply_host_parts, which copies each part
+    # in, multiplies and copies the result out on three streams so the parts
+    # overlap, and returns with every Y on the host; then PageRank runs on the
+    # device and its ranks are read back to pinned host memory.
     e2e = None
     if not args.no_e2e:
-        Xp = {k: X[k].cpu().pin_memory() for k in ks}
-        Yp = {k: torch.empty((N, k), dtype=torch.float32).pin_memory() for k in ks}
-        Xd = {k: torch.empty_like(X[k]) for k in ks}
+        Xp = [X[k].cpu().pin_memory() for k in ks]
+        Yp = [torch.empty((N, k), dtype=torch.float32).pin_memory() for k in ks]
         xp_host = torch.empty(N, dtype=torch.float32).pin_memory()
-        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-
-        # per-buffer order across steps: the next copy into Xd[k] waits for the
-        # product that read it, the next product into Y[k] for the copy out of
-        # it, the next PageRank into xpr for the copy of its ranks; nothing else
-        # waits, so consecutive steps overlap on the link in both directions
-        ev_mm, ev_out, ev_rank = {}, {}, [None]
 
         def e2e_step():
-            done_in = {}
-            for k in ks:
-                with torch.cuda.stream(s_in):
-                    if k in ev_mm:
-                        s_in.wait_event(ev_mm[k])
-                    Xd[k].copy_(Xp[k], non_blocking=True)
-                    done_in[k] = torch.cuda.Event()
-                    done_in[k].record(s_in)
-            if args.pagerank_iters:          # needs no host input: runs while X streams in
-                if ev_rank[0] is not None:
-                    stream.wait_event(ev_rank[0])
-                h.pagerank(0.85, args.pagerank_iters, x=xpr)
-                with torch.cuda.stream(s_out):
-                    s_out.wait_stream(stream)
-                    xp_host.copy_(xpr, non_blocking=True)
-                    ev_rank[0] = torch.cuda.Event()
-                    ev_rank[0].record(s_out)
-            for k in ks:
-                stream.wait_event(done_in[k])
-                if k in ev_out:
-                    stream.wait_event(ev_out[k])
-                h.apply(Xd[k], Y=Y[k], stream=stream)
-                ev_mm[k] = torch.cuda.Event()
-                ev_mm[k].record(stream)
-                with torch.cuda.stream(s_out):
-                    s_out.wait_event(ev_mm[k])
-                    Yp[k].copy_(Y[k], non_blocking=True)
-                    ev_out[k] = torch.cuda.Event()
-                    ev_out[k].record(s_out)
+            h.apply_host_parts(Xp, Yp, transpose=args.transpose, stream=stream)
+            if args.pagerank_iters:
+                h.pagerank(0.85, args.pagerank_iters, x=xpr, stream=stream)
+                xp_host.copy_(xpr, non_blocking=True)
         for _ in range(2):
             e2e_step()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
             e2e_step()
-        stream.wait_stream(s_out)            # every copy out is inside the timed region
-        stream.wait_stream(s_in)
         e1.record(stream)
         torch.cuda.synchronize()
-        te = e0.elapsed_time(e1) / 1e3
-        ok = all(torch.equal(Yp[k], Y[k].cpu()) for k in ks)
+        te = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0)
+        ok = all(torch.equal(Yp[i], Y[k].cpu()) for i, k in enumerate(ks))
+        if args.pagerank_iters:
+            ok = ok and torch.equal(xp_host, xpr.cpu())
         hb = sum(N * k * 4 for k in ks)
         db = hb + (N * 4 if args.pagerank_iters else 0)
         e2e = {"value": world * nnz * (len(ks) + args.pagerank_iters) * reps / te, "unit": UNIT,
                "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db, "ms_per_step": 1e3 * te / reps,
-               "results_match_device": ok}
-        del Xp, Yp, Xd
+               "api": "spmm_apply_host_parts (host X and Y, one part per k) + spmm_pagerank + rank read-back",
+               "results_match_device": bool(ok)}
+        del Xp, Yp
 
     # ---- CPU baseline: the oracle on a bounded row sample, all host cores
     cpu = None
@@ -967,6 +1010,12 @@ def main():
         cpu = {"value": (nz * len(ks) + pr * nnz) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{len(rows)} seeded rows ({nz} nonzeros) of the scale-{args.scale} graph, FP64, "
                          f"every k in the sweep, plus {pr} full PageRank iteration (serial) ({dt:.1f} s)"}
+        # the same oracle on one host thread (a smaller sample, SpMM rows only)
+        rows1, nz1 = cpu_sample_rows(A, max(nz // max(threads, 1), 10_000), seed=10)
+        dt1 = run_cpu_oracle(A, Xh, ks, rows1, 1)
+        cpu["single_thread"] = {"value": nz1 * len(ks) / dt1, "unit": UNIT, "cores": 1,
+                                "sample": f"{len(rows1)} seeded rows ({nz1} nonzeros), every k in the sweep, "
+                                          f"no PageRank ({dt1:.1f} s)"}
 
     if rank == 0:
         line = {
@@ -982,8 +1031,9 @@ def main():
             "bf16": bf16,
             "parity_max_err_over_absprod": parity,
             "roofline": {"bound": "hbm", "achieved": dom["alg_GBps"], "peak": peak_gbs, "unit": "GB/s",
-                         "frac": dom["roofline_frac"], "traffic": dom.get("traffic"), "kernel": dom_name,
-                         "peak_kind": peak_kind},
+                         "frac": dom["roofline_frac"], "traffic": traffic, "traffic_source": traffic_src,
+                         "kernel": dom_name, "peak_kind": peak_kind,
+                         "alg_bytes_per_launch": alg_bytes(nnz, N, N, kdom, 4)},
             "pagerank": pagerank,
             "gather_ceiling": {"per_k": ceilings, "pagerank": pr_ceiling,
                                "note": "rows/s of gathers alone: uniform = random rows of an X-sized table "

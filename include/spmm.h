@@ -499,8 +499,12 @@ int spmm_static_status(void* stream);
  *   x0         device float[N] start vector, or NULL for 1/N
  *   residuals  host double[iters] or NULL: sum_u |x'(u) - x(u)| of each iteration (FP64)
  * Synchronises `stream` first, then runs on an internal stream and returns
- * when the ranks are ready.  Allocates and frees its workspace (4 floats per
- * vertex).  Errors: SPMM_ERR_ARG (NULL, non-square, values present, no
+ * when the ranks are ready.  The first call allocates a workspace (about 12
+ * bytes per vertex) and an internal stream, and captures iterations
+ * 2..iters as a CUDA graph; the handle keeps them until spmm_destroy, and a
+ * later call with the same x, damping and iters only launches the graph
+ * (another x, damping or iters is captured anew).  Calls on one handle must
+ * not overlap.  Errors: SPMM_ERR_ARG (NULL, non-square, values present, no
  * transpose, bad d or iters), SPMM_ERR_TIMEOUT, SPMM_ERR_OOM, SPMM_ERR_CUDA.
  */
 int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float* x, const float* x0, double* residuals,
@@ -589,34 +593,6 @@ int spmm_replan(spmm_mat_t A, const spmm_opts* opts, int32_t transpose, void* st
  */
 int spmm_autotune(spmm_mat_t A, int32_t k, spmm_dtype xtype, int32_t transpose, const spmm_opts* candidates,
                   int32_t n_candidates, int32_t reps, int32_t* best_index, double* times_ms, void* stream);
-
-/*
- * spmm_probe_gather -- diagnostic: the measured rate of uniformly random row
- * gathers on this GPU, the practical ceiling of the SpMM's dominant cost
- * (one X row per nonzero).  Gathers rows of row_bytes (a power of two,
- * 4..256) at random row indices from a zero-filled table of table_bytes
- * (4 KiB .. 64 GiB; below the L2 size the rows come from L2, above it from
- * DRAM), eight loads in flight per lane, about 4 GB gathered.
- *   rows_per_s, bytes_per_s   host out
- * Synchronises `stream`; allocates its table.  Not a paper operation.
- */
-int spmm_probe_gather(int64_t table_bytes, int32_t row_bytes, double* rows_per_s, double* bytes_per_s,
-                      void* stream);
-
-/*
- * spmm_probe_gather_cols -- diagnostic: the gather ceiling of one matrix.
- * Replays the handle's own column-index stream (forward, or the transpose if
- * `transpose` != 0) in storage order, gathering for every stored entry one
- * row of row_bytes (a multiple of 4, 4..256; 4*k for an FP32 X of k columns)
- * from a zero table of n_cols rows, and nothing else of the SpMM.  Five runs
- * back to back (the table stays warm, as X does across iterations).
- *   rows_per_s   host out: stored entries per second
- *   bytes_per_s  host out: (row_bytes + 4) per entry per second
- * Synchronises `stream`; allocates its table.  SPMM_ERR_UNSUPPORTED for a
- * streaming handle.  Not a paper operation.
- */
-int spmm_probe_gather_cols(spmm_mat_t A, int32_t transpose, int32_t row_bytes, double* rows_per_s,
-                           double* bytes_per_s, void* stream);
 
 /*
  * spmm_svds -- the nsv largest singular values of A (any shape) and their

@@ -1,5 +1,7 @@
 """Build libspmm.so in place: every CUDA/C++ translation unit under csrc/ is
-compiled for sm_103a in parallel, then linked into one shared library."""
+compiled for sm_103a in parallel, then linked into one shared library.  The
+gather-ceiling diagnostics under diag/ are linked into libspmm_probe.so,
+outside the library's interface."""
 from __future__ import annotations
 
 import os
@@ -13,11 +15,13 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libspmm.so")
+DIAG = os.path.join(HERE, "diag")
+PROBE_LIB = os.path.join(HERE, "libspmm_probe.so")
 OBJ = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-              "--expt-relaxed-constexpr"]
+              "-I", os.path.join(HERE, "diag"), "--expt-relaxed-constexpr"]
 
 
 def nvcc() -> str:
@@ -34,13 +38,14 @@ def sources() -> list[str]:
 def _deps() -> list[str]:
     out = [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     out += [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    out += [os.path.join(DIAG, f) for f in os.listdir(DIAG)]
     return out
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(PROBE_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB))
     return all(os.path.getmtime(p) <= t for p in _deps() + [__file__])
 
 
@@ -64,11 +69,19 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return obj
 
     srcs = sources()
-    with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    diag = sorted(os.path.join(DIAG, f) for f in os.listdir(DIAG) if f.endswith(".cu"))
+    with ThreadPoolExecutor(max_workers=min(len(srcs) + len(diag), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, srcs + diag))
+    lib_objs, diag_objs = objs[:len(srcs)], objs[len(srcs):]
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *lib_objs, "-lcudart"])
     os.replace(tmp, LIB)
+    # the diagnostics: a library of their own that uses libspmm.so's handle
+    # and error string (found beside it at run time)
+    tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *diag_objs, "-L", HERE, "-lspmm", "-lcudart",
+                           "-Xlinker", "-rpath,$ORIGIN"])
+    os.replace(tmp, PROBE_LIB)
     return LIB
 
 

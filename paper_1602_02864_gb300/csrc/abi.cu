@@ -658,6 +658,7 @@ cudaError_t launch_rows(const FwdArgs& a, int32_t xtype, int vmode, int vec, int
 // the applications built on it.
 int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
               int64_t ldy, cudaStream_t s) {
+    NvtxRange range(transpose ? "spmm_apply A^T X" : "spmm_apply A X");
     if (A->streaming && !transpose) return stream_apply(A, X, ldx, k, xtype, Y, ldy, s);
     const DevCSR& d = transpose ? A->tr : A->fwd;
     if (d.n_rows == 0) return SPMM_OK;
@@ -762,6 +763,7 @@ extern "C" int spmm_destroy(spmm_mat_t A) {
     cudaError_t e = cudaDeviceSynchronize();
     if (A->streaming) stream_release(A);
     hostio_release(A);
+    pagerank_release(A);
     cudaFree(A->xperm);
     free_dev(A->fwd);
     free_dev(A->tr);
@@ -879,6 +881,7 @@ extern "C" int spmm_replan(spmm_mat_t A, const spmm_opts* opts, int32_t transpos
     if (A->streaming) { set_error("spmm_replan: not available for streaming handles"); return SPMM_ERR_UNSUPPORTED; }
     if (transpose && !A->has_tr) { set_error("spmm_replan: no transposed copy"); return SPMM_ERR_ARG; }
     const Params p = resolve_params(opts);
+    pagerank_invalidate(A);   // its graph holds the old plan's task list and scratch
     const int rc = replan_orientation(transpose ? A->tr : A->fwd, p, (cudaStream_t)stream, &A->device_bytes);
     if (rc == SPMM_OK) {
         // the L2 policy and compensation are launch parameters shared by both orientations

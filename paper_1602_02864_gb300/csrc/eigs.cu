@@ -274,6 +274,7 @@ static int eigs_impl(spmm_mat_t S, int op, int32_t nev, int32_t block, int32_t m
                      double tol, spmm_dtype xtype, const double* V0, double* evals, double* evecs, double* resid,
                      int32_t* restarts_out, void* stream) {
     if (!S || !V0 || !evals) { set_error("spmm_eigs: NULL argument"); return SPMM_ERR_ARG; }
+    NvtxRange range(op ? "spmm_svds" : "spmm_eigs");
     const int64_t n = op ? S->fwd.n_cols : S->fwd.n_rows;
     if (op == 0 && (S->fwd.n_cols != n || n < 1)) { set_error("spmm_eigs: the matrix must be square"); return SPMM_ERR_ARG; }
     if (op == 1 && !S->has_tr) { set_error("spmm_svds: needs SPMM_WANT_TRANSPOSE at create"); return SPMM_ERR_ARG; }

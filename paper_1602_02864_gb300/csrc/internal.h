@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -10,6 +11,15 @@
 #include "spmm.h"
 
 namespace spmm {
+
+// An NVTX range for the scope of one call or step (visible in Nsight
+// Systems timelines; free when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Warp tasks, in natural row order, cover every row exactly once:
 //   desc = int4 {r0, x, lo32(e0), hi32(e0)}, e0 = first nonzero of the task,
@@ -133,6 +143,23 @@ struct Params {
 }  // namespace spmm
 
 namespace spmm {
+// PageRank state kept by a handle after its first spmm_pagerank call: the
+// workspace, an internal stream and the CUDA graph of iterations 2..iters,
+// reused while (x, damping, iters) stay the same
+struct PrCache {
+    float *inv_deg = nullptr, *z = nullptr, *y = nullptr;
+    double *part = nullptr, *scal = nullptr, *dres = nullptr;
+    int32_t nblk = 0, dres_cap = 0;
+    cudaStream_t s = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    float* x = nullptr;
+    double damping = -1.0;
+    int32_t iters = -1;
+};
+void pagerank_release(spmm_mat* A);
+// drop the captured PageRank graph (the plan or a buffer it uses changed)
+void pagerank_invalidate(spmm_mat* A);
+
 // device buffers, streams and events of spmm_apply_host (created on first use)
 struct HostIO {
     void* x[2] = {nullptr, nullptr};
@@ -160,6 +187,7 @@ struct spmm_mat {
     spmm::HostIO hio;
     void* xperm = nullptr;      // SPMM_REORDER: X with its rows in relabelled order (grow-only)
     size_t xperm_bytes = 0;
+    spmm::PrCache pr;           // spmm_pagerank's workspace and graph (after its first call)
 };
 
 namespace spmm {

@@ -175,6 +175,7 @@ using namespace spmm;
 extern "C" int spmm_nmf(spmm_mat_t A, int32_t k, int32_t steps, float* W, float* Ht, spmm_dtype ftype, double eps,
                         double* objective, void* stream) {
     if (!A || !W || !Ht) { set_error("spmm_nmf: NULL argument"); return SPMM_ERR_ARG; }
+    NvtxRange range("spmm_nmf");
     if (k < 1 || k > kMaxK || steps < 0 || !(eps >= 0.0)) {
         set_error("spmm_nmf: need 1 <= k <= 64, steps >= 0, eps >= 0");
         return SPMM_ERR_ARG;

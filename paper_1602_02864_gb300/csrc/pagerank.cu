@@ -9,9 +9,10 @@
 // One iteration = the task kernel on A^T (k = 1, float32) + one fused
 // elementwise kernel (new ranks, the next z = x' * (1/L), FP64 per-block
 // partial sums of the L1 change and of the dangling mass) + a one-block kernel
-// adding the partials in a fixed order.  All iterations are captured into one CUDA graph and
-// launched once.  Ranks are float32; every reduction is FP64 and run-to-run
-// deterministic.
+// adding the partials in a fixed order.  Iterations 2..iters are one CUDA
+// graph; the handle keeps it with the workspace, so a later call with the
+// same x, damping and iteration count only launches it.  Ranks are float32;
+// every reduction is FP64 and run-to-run deterministic.
 #include <vector>
 
 #include "internal.h"
@@ -142,6 +143,60 @@ __global__ void pr_reduce_kernel(const double* __restrict__ part_dang, const dou
 
 using namespace spmm;
 
+namespace spmm {
+
+void pagerank_release(spmm_mat* A) {
+    PrCache& c = A->pr;
+    if (c.exec) cudaGraphExecDestroy(c.exec);
+    if (c.s) cudaStreamDestroy(c.s);
+    cudaFree(c.inv_deg);
+    cudaFree(c.z);
+    cudaFree(c.y);
+    cudaFree(c.part);
+    cudaFree(c.scal);
+    cudaFree(c.dres);
+    c = PrCache{};
+}
+
+void pagerank_invalidate(spmm_mat* A) {
+    PrCache& c = A->pr;
+    if (c.exec) cudaGraphExecDestroy(c.exec);
+    c.exec = nullptr;
+    c.x = nullptr;
+    c.damping = -1.0;
+    c.iters = -1;
+}
+
+// The workspace of an n-vertex PageRank with room for `iters` residuals.
+static cudaError_t pr_reserve(PrCache& c, int64_t n, int32_t iters, int nblk) {
+    cudaError_t e = cudaSuccess;
+    if (!c.inv_deg) {
+        if ((e = cudaMalloc((void**)&c.inv_deg, n * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&c.z, n * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&c.y, n * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&c.part, 2 * (size_t)nblk * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&c.scal, 8 * sizeof(double))) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&c.s, cudaStreamNonBlocking)) != cudaSuccess)
+            return e;
+        c.nblk = nblk;
+    }
+    if (iters > c.dres_cap) {
+        cudaFree(c.dres);
+        c.dres = nullptr;
+        c.dres_cap = 0;
+        if ((e = cudaMalloc((void**)&c.dres, (size_t)iters * sizeof(double))) != cudaSuccess) return e;
+        c.dres_cap = iters;
+        if (c.exec) {                          // its residual pointers are gone
+            cudaGraphExecDestroy(c.exec);
+            c.exec = nullptr;
+            c.iters = -1;
+        }
+    }
+    return e;
+}
+
+}  // namespace spmm
+
 extern "C" int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float* x, const float* x0,
                              double* residuals, void* stream) {
     if (!A || !x) { set_error("spmm_pagerank: NULL argument"); return SPMM_ERR_ARG; }
@@ -164,60 +219,68 @@ extern "C" int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float*
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "spmm_pagerank: device query");
-    const int nblk = sms * 8;
-    // workspace: 1/out-degree, z, y (float n each), partials (2 x nblk), scalar, residuals
-    float *inv_deg = nullptr, *z = nullptr, *y = nullptr;
-    double *part = nullptr, *scal = nullptr, *dres = nullptr;
-    cudaStream_t s = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    PrCache& c = A->pr;
     int rc = SPMM_OK;
+    NvtxRange range("spmm_pagerank");
     auto fail = [&](cudaError_t err, const char* what) { rc = cuda_fail(err, what); };
     do {
         if ((e = cudaStreamSynchronize(user)) != cudaSuccess) { fail(e, "spmm_pagerank: stream"); break; }
-        if ((e = cudaMalloc((void**)&inv_deg, n * sizeof(float))) != cudaSuccess ||
-            (e = cudaMalloc((void**)&z, n * sizeof(float))) != cudaSuccess ||
-            (e = cudaMalloc((void**)&y, n * sizeof(float))) != cudaSuccess ||
-            (e = cudaMalloc((void**)&part, 2 * (size_t)nblk * sizeof(double))) != cudaSuccess ||
-            (e = cudaMalloc((void**)&scal, 8 * sizeof(double))) != cudaSuccess ||
-            (e = cudaMalloc((void**)&dres, (size_t)(iters > 0 ? iters : 1) * sizeof(double))) != cudaSuccess) {
+        if ((e = pr_reserve(c, n, iters, sms * 8)) != cudaSuccess) {
             fail(e, "spmm_pagerank: workspace");
+            pagerank_release(A);
             break;
         }
-        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) {
-            fail(e, "spmm_pagerank: stream create");
-            break;
-        }
-        // set-up outside the graph
-        pr_init_kernel<<<nblk, kPrThreads, 0, s>>>(A->fwd.row_ptr, n, inv_deg, x, x0);
-        pr_scale_kernel<<<nblk, kPrThreads, 0, s>>>(x, inv_deg, n, z, part);
-        pr_reduce_kernel<<<1, kPrThreads, 0, s>>>(part, nullptr, nblk, scal, nullptr);
+        const int nblk = c.nblk;
+        cudaStream_t s = c.s;
+        // set-up outside the graph: 1/L, the start vector, z and its dangling mass
+        pr_init_kernel<<<nblk, kPrThreads, 0, s>>>(A->fwd.row_ptr, n, c.inv_deg, x, x0);
+        pr_scale_kernel<<<nblk, kPrThreads, 0, s>>>(x, c.inv_deg, n, c.z, c.part);
+        pr_reduce_kernel<<<1, kPrThreads, 0, s>>>(c.part, nullptr, nblk, c.scal, nullptr);
         if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "spmm_pagerank: init"); break; }
         if (iters > 0) {
             // the first iteration runs outside the graph, so the task kernel's
             // one-time launch set-up (attributes, occupancy) happens before capture
-            if ((rc = apply_dev(A, 1, z, 1, 1, SPMM_F32, y, 1, s)) != SPMM_OK) break;
-            pr_update_kernel<<<nblk, kPrThreads, 0, s>>>(y, x, inv_deg, n, damping, scal, z, part + nblk, part);
-            pr_reduce_kernel<<<1, kPrThreads, 0, s>>>(part, part + nblk, nblk, scal, dres);
+            if ((rc = apply_dev(A, 1, c.z, 1, 1, SPMM_F32, c.y, 1, s)) != SPMM_OK) break;
+            pr_update_kernel<<<nblk, kPrThreads, 0, s>>>(c.y, x, c.inv_deg, n, damping, c.scal, c.z, c.part + nblk,
+                                                         c.part);
+            pr_reduce_kernel<<<1, kPrThreads, 0, s>>>(c.part, c.part + nblk, nblk, c.scal, c.dres);
             if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "spmm_pagerank: first iteration"); break; }
         }
         if (iters > 1) {
-            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "spmm_pagerank: first iteration"); break; }
-            if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
-                fail(e, "spmm_pagerank: capture");
-                break;
-            }
-            for (int32_t t = 1; t < iters && rc == SPMM_OK; ++t) {
-                rc = apply_dev(A, 1, z, 1, 1, SPMM_F32, y, 1, s);
+            // iterations 2..iters: one graph, captured on the first call with
+            // this x, damping and iteration count and relaunched after that
+            if (!(c.exec && c.x == x && c.damping == damping && c.iters == iters)) {
+                if (c.exec) {
+                    cudaGraphExecDestroy(c.exec);
+                    c.exec = nullptr;
+                }
+                c.iters = -1;
+                if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "spmm_pagerank: first iteration"); break; }
+                if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+                    fail(e, "spmm_pagerank: capture");
+                    break;
+                }
+                for (int32_t t = 1; t < iters && rc == SPMM_OK; ++t) {
+                    rc = apply_dev(A, 1, c.z, 1, 1, SPMM_F32, c.y, 1, s);
+                    if (rc != SPMM_OK) break;
+                    pr_update_kernel<<<nblk, kPrThreads, 0, s>>>(c.y, x, c.inv_deg, n, damping, c.scal, c.z,
+                                                                 c.part + nblk, c.part);
+                    pr_reduce_kernel<<<1, kPrThreads, 0, s>>>(c.part, c.part + nblk, nblk, c.scal, c.dres + t);
+                }
+                cudaGraph_t graph = nullptr;
+                cudaError_t ec = cudaStreamEndCapture(s, &graph);
+                if (rc == SPMM_OK && ec != cudaSuccess) fail(ec, "spmm_pagerank: end capture");
+                if (rc == SPMM_OK && (e = cudaGraphInstantiate(&c.exec, graph, 0)) != cudaSuccess) {
+                    c.exec = nullptr;
+                    fail(e, "spmm_pagerank: instantiate");
+                }
+                if (graph) cudaGraphDestroy(graph);
                 if (rc != SPMM_OK) break;
-                pr_update_kernel<<<nblk, kPrThreads, 0, s>>>(y, x, inv_deg, n, damping, scal, z, part + nblk, part);
-                pr_reduce_kernel<<<1, kPrThreads, 0, s>>>(part, part + nblk, nblk, scal, dres + t);
+                c.x = x;
+                c.damping = damping;
+                c.iters = iters;
             }
-            cudaError_t ec = cudaStreamEndCapture(s, &graph);
-            if (rc != SPMM_OK) break;
-            if (ec != cudaSuccess) { fail(ec, "spmm_pagerank: end capture"); break; }
-            if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) { fail(e, "spmm_pagerank: instantiate"); break; }
-            if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) { fail(e, "spmm_pagerank: launch"); break; }
+            if ((e = cudaGraphLaunch(c.exec, s)) != cudaSuccess) { fail(e, "spmm_pagerank: launch"); break; }
         }
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "spmm_pagerank: run"); break; }
         int32_t st = 0;
@@ -232,19 +295,11 @@ extern "C" int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float*
             break;
         }
         if (residuals && iters > 0 &&
-            (e = cudaMemcpy(residuals, dres, (size_t)iters * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            (e = cudaMemcpy(residuals, c.dres, (size_t)iters * sizeof(double), cudaMemcpyDeviceToHost)) !=
+                cudaSuccess) {
             fail(e, "spmm_pagerank: residuals");
             break;
         }
     } while (0);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    if (s) cudaStreamDestroy(s);
-    cudaFree(inv_deg);
-    cudaFree(z);
-    cudaFree(y);
-    cudaFree(part);
-    cudaFree(scal);
-    cudaFree(dres);
     return rc;
 }

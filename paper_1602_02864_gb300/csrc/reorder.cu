@@ -69,6 +69,7 @@ int reorder_reserve(spmm_mat* A, int64_t n_in, int32_t k, int32_t xtype, cudaStr
         return SPMM_ERR_UNSUPPORTED;
     }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "reorder: pending work");
+    pagerank_invalidate(A);   // its graph writes the old buffer
     cudaFree(A->xperm);
     A->xperm = nullptr;
     A->xperm_bytes = 0;

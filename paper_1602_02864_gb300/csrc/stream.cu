@@ -201,6 +201,7 @@ int stream_apply(const spmm_mat* A, const void* X, int64_t ldx, int32_t k, int32
     int rc = SPMM_OK;
     cudaError_t e = cudaSuccess;
     for (size_t bi = 0; bi < S.blocks.size(); ++bi) {
+        NvtxRange brange("spmm_apply stream block");
         const StreamBlock& b = S.blocks[bi];
         const int slot = (int)(bi & 1);
         if (S.fail_block > 0 && (size_t)(S.fail_block - 1) == bi) {

@@ -208,6 +208,7 @@ extern "C" int spmm_apply_host(spmm_mat_t A, const void* X, int64_t ldx, int32_t
                                int64_t ldy, int32_t transpose, int32_t group_cols, int64_t budget_bytes,
                                int32_t* groups_out, void* stream) {
     int rc;
+    NvtxRange range("spmm_apply_host");
     if ((rc = check_common(A, xtype, transpose, "spmm_apply_host")) != SPMM_OK) return rc;
     if (p < 1 || ldx < p || ldy < p || group_cols < 0 || group_cols > kMaxK || budget_bytes < 0) {
         set_error("spmm_apply_host: need p >= 1, ldx >= p, ldy >= p, 0 <= group_cols <= 64, budget >= 0");
@@ -245,6 +246,7 @@ extern "C" int spmm_apply_host(spmm_mat_t A, const void* X, int64_t ldx, int32_t
 extern "C" int spmm_apply_host_parts(spmm_mat_t A, const void* const* X_parts, float* const* Y_parts,
                                      const int32_t* part_cols, int32_t n_parts, spmm_dtype xtype, int32_t transpose,
                                      void* stream) {
+    NvtxRange range("spmm_apply_host_parts");
     int rc;
     if ((rc = check_common(A, xtype, transpose, "spmm_apply_host_parts")) != SPMM_OK) return rc;
     if (n_parts < 1 || !X_parts || !Y_parts || !part_cols) {

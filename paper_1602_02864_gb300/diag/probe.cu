@@ -15,6 +15,7 @@
 // reductions or stores).  On a power-law graph the hot columns stay in L2,
 // so this, not the uniform probe, is the gather ceiling for that matrix.
 #include "internal.h"
+#include "spmm_probe.h"
 
 namespace spmm {
 

@@ -104,12 +104,6 @@ _lib.spmm_autotune.restype = ctypes.c_int
 _lib.spmm_create_tiles.argtypes = [ctypes.POINTER(_P), _i64, _i64, _i32, _i64, ctypes.POINTER(spmm_tile_desc),
                                    ctypes.c_int, _u32, ctypes.POINTER(spmm_opts), _P]
 _lib.spmm_create_tiles.restype = ctypes.c_int
-_lib.spmm_probe_gather.argtypes = [_i64, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
-                                   _P]
-_lib.spmm_probe_gather.restype = ctypes.c_int
-_lib.spmm_probe_gather_cols.argtypes = [_P, _i32, _i32, ctypes.POINTER(ctypes.c_double),
-                                        ctypes.POINTER(ctypes.c_double), _P]
-_lib.spmm_probe_gather_cols.restype = ctypes.c_int
 _lib.spmm_svds.argtypes = [_P, _i32, _i32, _i32, _i32, ctypes.c_double, ctypes.c_int, _P, _P, _P, _P, _P, _P]
 _lib.spmm_svds.restype = ctypes.c_int
 _lib.spmm_vpart_cols.argtypes = [_i64, _i64, _i32, ctypes.c_int, _i64, _P]
@@ -421,23 +415,6 @@ def _host_matrix(M):
     if code is None:
         raise ValueError(f"unsupported host dtype {M.dtype}")
     return code, M.stride(0), M.shape[1], _P(M.data_ptr())
-
-
-def spmm_probe_gather(table_bytes, row_bytes, stream=None):
-    """(rows/s, bytes/s) of uniformly random row gathers from a table."""
-    r, b = ctypes.c_double(0), ctypes.c_double(0)
-    _check(_lib.spmm_probe_gather(int(table_bytes), int(row_bytes), ctypes.byref(r), ctypes.byref(b),
-                                  _stream_handle(stream)))
-    return r.value, b.value
-
-
-def spmm_probe_gather_cols(h, transpose, row_bytes, stream=None):
-    """(rows/s, bytes/s) of gathering one table row per stored entry of the
-    handle's column-index stream."""
-    r, b = ctypes.c_double(0), ctypes.c_double(0)
-    _check(_lib.spmm_probe_gather_cols(h, int(bool(transpose)), int(row_bytes), ctypes.byref(r), ctypes.byref(b),
-                                       _stream_handle(stream)))
-    return r.value, b.value
 
 
 def spmm_svds(h, nsv, V0, block=16, max_basis=64, max_restarts=100, tol=1e-6, xtype=SPMM_F32, right_vecs=None,

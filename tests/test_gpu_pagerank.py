@@ -102,3 +102,35 @@ def test_compensated_plan_gives_the_same_ranks(sp, opts):
     assert np.all(np.abs(xf - xr) <= 1e-5 * xr + 1e-12)
     hf.close()
     hc.close()
+
+
+def test_pagerank_cached_graph_follows_its_inputs(sp):
+    """The handle keeps the captured iterations: a repeated call relaunches
+    them, and another output vector, damping, iteration count, start vector
+    or plan (spmm_replan) still gives the oracle's ranks."""
+    import torch
+    A = synth.rmat_csr(13, seed=21)
+    h = handle(sp, A)
+    try:
+        xa = torch.empty(A.n_rows, device="cuda")
+        xb = torch.empty(A.n_rows, device="cuda")
+        x0 = torch.from_numpy(synth.dense(A.n_rows, 1, seed=4, mode="unit")[:, 0]).cuda()
+        x0 /= x0.sum()
+        cases = [(xa, 0.85, 30, None), (xa, 0.85, 30, None), (xb, 0.85, 30, None), (xa, 0.5, 30, None),
+                 (xa, 0.85, 7, None), (xa, 0.85, 30, x0), (xa, 0.85, 1, None), (xa, 0.85, 0, None),
+                 ("replan", None, None, None), (xa, 0.85, 30, None)]
+        for x, d, it, start in cases:
+            if isinstance(x, str):
+                sp.spmm_replan(h.handle, sp.spmm_opts(task_nnz=128, short_max=15), 1)
+                continue
+            _, res = h.pagerank(d, it, x=x, x0=start)
+            s0 = None if start is None else start.double().cpu().numpy()
+            xr, resr = oracle.pagerank(A.n_rows, A.row_ptr, A.col_idx, d, it, x0=s0)
+            xg = x.cpu().numpy().astype(np.float64)
+            assert np.all(np.abs(xg - xr) <= 1e-5 * xr + 1e-12), (d, it)
+            assert len(res) == it
+            if it:
+                np.testing.assert_allclose(res, resr, rtol=1e-3, atol=4 * 2.0 ** -24)
+        h.sync_status()
+    finally:
+        h.close()

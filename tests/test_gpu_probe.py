@@ -8,8 +8,13 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def sp():
-    from paper_1602_02864_gb300 import spmm
-    return spmm
+    """The library binding with the diagnostics' two calls beside it."""
+    import types
+    from paper_1602_02864_gb300 import probe, spmm
+    ns = types.SimpleNamespace(**{n: getattr(spmm, n) for n in dir(spmm) if not n.startswith("__")})
+    ns.spmm_probe_gather = probe.spmm_probe_gather
+    ns.spmm_probe_gather_cols = probe.spmm_probe_gather_cols
+    return ns
 
 
 def test_uniform_probe(sp):

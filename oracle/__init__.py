@@ -13,9 +13,13 @@ Each function is the plain definition from the paper, summed in double:
 * ``pagerank``    the Section 4.1 update rule, dangling mass spread uniformly
 * ``nmf``         the Section 4.3 multiplicative updates (H first, then W)
 * ``lanczos``     top eigenpairs of a symmetric sparse matrix (Section 4.2 uses
-                  a Krylov eigensolver; here block Lanczos, full
-                  re-orthogonalisation, Jacobi on the projected matrix)
-* ``jacobi_eigh`` the dense symmetric eigen-decomposition used by ``lanczos``
+                  a Krylov eigensolver; here block Lanczos with full
+                  re-orthogonalisation)
+* ``svds``        top singular values (Section 5.5.2) by the same Lanczos on
+                  A^T A, applied as two products
+* ``sym_eigh``    the dense symmetric eigen-decomposition of the projected
+                  matrix: Householder tridiagonalisation, Sturm bisection,
+                  inverse iteration
 """
 from __future__ import annotations
 
@@ -57,8 +61,9 @@ def _load():
             lib.oracle_spmm_t_rows.argtypes = [i64, P, P, P, i32, P, i32, i64, i32, P, i64, P]
             lib.oracle_pagerank.argtypes = [i64, P, P, f64, i32, P, P]
             lib.oracle_nmf.argtypes = [i64, i64, P, P, P, i32, i32, i32, f64, P, P, P]
-            lib.oracle_jacobi_eigh.argtypes = [i32, P, P, P]
-            lib.oracle_lanczos.argtypes = [i64, P, P, P, i32, i32, i32, P, i32, P, P]
+            lib.oracle_sym_eigh.argtypes = [i32, P, P, P]
+            lib.oracle_sym_eigh.restype = i32
+            lib.oracle_lanczos.argtypes = [i64, i64, P, P, P, i32, i32, i32, i32, P, i32, P, P]
             lib.oracle_lanczos.restype = i32
             _lib = lib
     return _lib
@@ -77,7 +82,7 @@ class using_library:
         self._saved = _lib
         lib = ctypes.CDLL(self.path)
         for name in ("oracle_num_threads", "oracle_spmm", "oracle_spmm_rows", "oracle_spmm_t_rows",
-                     "oracle_pagerank", "oracle_nmf", "oracle_jacobi_eigh", "oracle_lanczos"):
+                     "oracle_pagerank", "oracle_nmf", "oracle_sym_eigh", "oracle_lanczos"):
             f, g = getattr(self._saved, name), getattr(lib, name)
             g.argtypes, g.restype = f.argtypes, f.restype
         with _lock:
@@ -193,24 +198,46 @@ def nmf(n_rows, n_cols, row_ptr, col_idx, values, W0, Ht0, steps, eps=1e-12):
     return W, Ht, obj
 
 
-def jacobi_eigh(M):
+def sym_eigh(M):
+    """All eigenpairs of a dense symmetric matrix: (evals ascending, V with
+    unit eigenvector columns), by Householder tridiagonalisation, Sturm
+    bisection and inverse iteration (oracle_sym_eigh)."""
     M = np.array(M, dtype=np.float64, order="C")
     m = M.shape[0]
     ev = np.zeros(m, dtype=np.float64)
     V = np.zeros((m, m), dtype=np.float64)
-    _load().oracle_jacobi_eigh(m, _p(M), _p(ev), _p(V))
+    if _load().oracle_sym_eigh(m, _p(M), _p(ev), _p(V)) != 0:
+        raise MemoryError("oracle_sym_eigh: allocation failed")
     return ev, V
 
 
 def lanczos(n, row_ptr, col_idx, values, Q0, nev, m_max):
-    """Top-nev eigenpairs (descending) of the symmetric CSR matrix S."""
+    """Top-nev eigenpairs (descending) of the symmetric n x n CSR matrix S:
+    (evals, vectors n x nev, basis size)."""
     rp, ci = _csr(row_ptr, col_idx)
     v, vt = _vals(values)
     Q0 = np.ascontiguousarray(Q0, dtype=np.float64)
     b = Q0.shape[1]
     ev = np.zeros(nev, dtype=np.float64)
     V = np.zeros((n, nev), dtype=np.float64)
-    m = _load().oracle_lanczos(n, _p(rp), _p(ci), _p(v), vt, b, int(m_max), _p(Q0), nev, _p(ev), _p(V))
+    m = _load().oracle_lanczos(n, n, _p(rp), _p(ci), _p(v), vt, 0, b, int(m_max), _p(Q0), nev, _p(ev), _p(V))
     if m < 0:
         raise MemoryError("oracle_lanczos: allocation failed")
     return ev, V, m
+
+
+def svds(n_rows, n_cols, row_ptr, col_idx, values, Q0, nsv, m_max):
+    """Top-nsv singular values (descending) of the n_rows x n_cols CSR matrix
+    A, from block Lanczos on A^T A applied as A q then A^T (A q): (singular
+    values, right singular vectors n_cols x nsv, basis size)."""
+    rp, ci = _csr(row_ptr, col_idx)
+    v, vt = _vals(values)
+    Q0 = np.ascontiguousarray(Q0, dtype=np.float64)
+    b = Q0.shape[1]
+    ev = np.zeros(nsv, dtype=np.float64)
+    V = np.zeros((n_cols, nsv), dtype=np.float64)
+    m = _load().oracle_lanczos(n_rows, n_cols, _p(rp), _p(ci), _p(v), vt, 1, b, int(m_max), _p(Q0), nsv, _p(ev),
+                               _p(V))
+    if m < 0:
+        raise MemoryError("oracle_lanczos: allocation failed")
+    return np.sqrt(np.maximum(ev, 0.0)), V, m

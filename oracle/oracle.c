@@ -15,9 +15,11 @@
  *                      (Section 4.1), dangling mass spread uniformly
  *   oracle_nmf         H <- H o (W^T A) / (W^T W H),  W <- W o (A H^T) / (W H H^T)
  *                      (Section 4.3, multiplicative updates, H first)
- *   oracle_lanczos     top eigenpairs of a symmetric sparse matrix (Section 4.2
- *                      needs eigenpairs; block Lanczos with full
- *                      re-orthogonalisation, cyclic Jacobi on the projection)
+ *   oracle_lanczos     top eigenpairs of a symmetric sparse matrix, or of A^T A
+ *                      for singular values (Sections 4.2, 5.5.2: block Lanczos
+ *                      with full re-orthogonalisation; the projection is
+ *                      diagonalised by oracle_sym_eigh: Householder
+ *                      tridiagonalisation, Sturm bisection, inverse iteration)
  * Types: vtype 0 = pattern (every stored entry is 1), 1 = float32, 2 = float64.
  *        xtype 1 = float32, 2 = float64.  Inputs are read in their own type and
  *        widened to double exactly.
@@ -226,61 +228,235 @@ void oracle_nmf(int64_t n_rows, int64_t n_cols, const int64_t* row_ptr, const in
 }
 
 /* ------------------------------------------------------------ eigensolver -- */
-/* Cyclic Jacobi eigen-decomposition of a dense symmetric m x m matrix M
- * (row-major, destroyed).  On return evals[i] are the eigenvalues and column i
- * of V (row-major m x m) the matching unit eigenvector.  Rotations annihilate
- * one off-diagonal pair at a time until the off-diagonal mass is negligible. */
-void oracle_jacobi_eigh(int32_t m, double* M, double* evals, double* V) {
+/* Dense symmetric eigenproblem, three textbook steps (any numerical linear
+ * algebra text; e.g. Golub & Van Loan, Matrix Computations, ch. 8):
+ *   1. Householder reduction M = H T H^T, T symmetric tridiagonal;
+ *   2. each eigenvalue of T by bisection on its Sturm count (the number of
+ *      negative pivots of the LDL^T factorisation of T - x I is the number of
+ *      eigenvalues below x);
+ *   3. each eigenvector of T by inverse iteration with T - lambda I factored
+ *      by Gaussian elimination with partial pivoting, vectors of nearby
+ *      eigenvalues re-orthogonalised, then mapped back by H. */
+
+/* Householder tridiagonalisation of the symmetric m x m row-major M
+ * (destroyed).  On return d (m) and e (m-1) hold T's diagonal and
+ * sub-diagonal, and H (row-major m x m, orthogonal) satisfies M = H T H^T. */
+static void house_tridiag(int32_t m, double* M, double* H, double* d, double* e) {
+    double* v = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    double* p = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     for (int32_t i = 0; i < m; ++i)
-        for (int32_t j = 0; j < m; ++j) V[i * m + j] = (i == j) ? 1.0 : 0.0;
-    for (int32_t sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int32_t i = 0; i < m; ++i)
-            for (int32_t j = 0; j < m; ++j) {
-                tot += M[i * m + j] * M[i * m + j];
-                if (i != j) off += M[i * m + j] * M[i * m + j];
-            }
-        if (off <= 1e-30 * (tot > 0 ? tot : 1.0) || off == 0.0) break;
-        for (int32_t p = 0; p < m; ++p)
-            for (int32_t q = p + 1; q < m; ++q) {
-                double apq = M[p * m + q];
-                if (apq == 0.0) continue;
-                double app = M[p * m + p], aqq = M[q * m + q];
-                double theta = (aqq - app) / (2.0 * apq);
-                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int32_t r = 0; r < m; ++r) {   /* M <- M J (columns p, q) */
-                    double mrp = M[r * m + p], mrq = M[r * m + q];
-                    M[r * m + p] = c * mrp - s * mrq;
-                    M[r * m + q] = s * mrp + c * mrq;
-                }
-                for (int32_t r = 0; r < m; ++r) {   /* M <- J^T M (rows p, q) */
-                    double mpr = M[p * m + r], mqr = M[q * m + r];
-                    M[p * m + r] = c * mpr - s * mqr;
-                    M[q * m + r] = s * mpr + c * mqr;
-                }
-                for (int32_t r = 0; r < m; ++r) {   /* V <- V J */
-                    double vrp = V[r * m + p], vrq = V[r * m + q];
-                    V[r * m + p] = c * vrp - s * vrq;
-                    V[r * m + q] = s * vrp + c * vrq;
-                }
-            }
+        for (int32_t j = 0; j < m; ++j) H[i * m + j] = (i == j) ? 1.0 : 0.0;
+    for (int32_t k = 0; k + 2 < m; ++k) {
+        /* reflect x = M[k+1.., k] onto alpha * e1 with P = I - 2 v v^T */
+        double xn = 0.0;
+        for (int32_t i = k + 1; i < m; ++i) xn += M[i * m + k] * M[i * m + k];
+        xn = sqrt(xn);
+        if (xn == 0.0) continue;
+        const double x0 = M[(k + 1) * m + k];
+        const double alpha = x0 > 0 ? -xn : xn;
+        double vn = 0.0;
+        for (int32_t i = k + 1; i < m; ++i) {
+            v[i] = M[i * m + k] - (i == k + 1 ? alpha : 0.0);
+            vn += v[i] * v[i];
+        }
+        vn = sqrt(vn);
+        if (vn == 0.0) continue;
+        for (int32_t i = k + 1; i < m; ++i) v[i] /= vn;
+        /* trailing block B <- P B P = B - 2 v p^T - 2 p v^T + 4 (v^T p) v v^T, p = B v */
+        double vp = 0.0;
+        for (int32_t i = k + 1; i < m; ++i) {
+            double acc = 0.0;
+            for (int32_t j = k + 1; j < m; ++j) acc += M[i * m + j] * v[j];
+            p[i] = acc;
+        }
+        for (int32_t i = k + 1; i < m; ++i) vp += v[i] * p[i];
+        for (int32_t i = k + 1; i < m; ++i)
+            for (int32_t j = k + 1; j < m; ++j)
+                M[i * m + j] += -2.0 * v[i] * p[j] - 2.0 * p[i] * v[j] + 4.0 * vp * v[i] * v[j];
+        /* column and row k: P x = alpha e1 */
+        for (int32_t i = k + 1; i < m; ++i) {
+            M[i * m + k] = (i == k + 1) ? alpha : 0.0;
+            M[k * m + i] = M[i * m + k];
+        }
+        /* H <- H P on columns k+1.. */
+        for (int32_t r = 0; r < m; ++r) {
+            double hv = 0.0;
+            for (int32_t j = k + 1; j < m; ++j) hv += H[r * m + j] * v[j];
+            for (int32_t j = k + 1; j < m; ++j) H[r * m + j] -= 2.0 * hv * v[j];
+        }
     }
-    for (int32_t i = 0; i < m; ++i) evals[i] = M[i * m + i];
+    for (int32_t i = 0; i < m; ++i) d[i] = M[i * m + i];
+    for (int32_t i = 0; i + 1 < m; ++i) e[i] = M[(i + 1) * m + i];
+    free(v);
+    free(p);
 }
 
-/* Block Lanczos with full re-orthogonalisation on a symmetric CSR matrix S
- * (n x n).  Q0 (n x b, row-major) is the start block.  Builds an orthonormal
- * Krylov basis of up to m_max columns (m_max a multiple of b), projects
- * T = Q^T S Q, diagonalises T by Jacobi, and returns the nev largest Ritz
- * values (descending) and their Ritz vectors (n x nev row-major).
- * Returns the basis size used, or -1 on allocation failure. */
-int32_t oracle_lanczos(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const void* val,
-                       int32_t vtype, int32_t b, int32_t m_max, const double* Q0, int32_t nev,
-                       double* evals, double* evecs) {
+/* Number of eigenvalues of tridiag(d, e) below x (Sturm count). */
+static int32_t sturm_below(int32_t m, const double* d, const double* e, double x, double tiny) {
+    int32_t cnt = 0;
+    double q = 1.0;
+    for (int32_t i = 0; i < m; ++i) {
+        const double ee = i > 0 ? e[i - 1] : 0.0;
+        q = d[i] - x - (i > 0 ? ee * ee / q : 0.0);
+        if (q == 0.0) q = -tiny;       /* a zero pivot: x is an eigenvalue of the leading block */
+        if (q < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+/* Solve (T - lam I) y = b in place (b -> y), T = tridiag(d, e), by Gaussian
+ * elimination with partial pivoting; a zero pivot is replaced by `tiny`. */
+static void tridiag_solve(int32_t m, const double* d, const double* e, double lam, double tiny, double* b,
+                          double* work) {
+    /* row i of the working matrix: diagonal a[i], first and second
+     * super-diagonals c1[i], c2[i]; sub-diagonal entries are eliminated */
+    double* a = work;
+    double* c1 = work + m;
+    double* c2 = work + 2 * m;
+    double* l = work + 3 * m;          /* multipliers */
+    int32_t* swapped = (int32_t*)(work + 4 * m);
+    for (int32_t i = 0; i < m; ++i) {
+        a[i] = d[i] - lam;
+        c1[i] = i + 1 < m ? e[i] : 0.0;
+        c2[i] = 0.0;
+    }
+    for (int32_t i = 0; i + 1 < m; ++i) {
+        /* rows i and i+1; the sub-diagonal entry of row i+1 is e[i] */
+        const double sub = e[i];
+        swapped[i] = fabs(sub) > fabs(a[i]);
+        if (swapped[i]) {
+            /* exchange rows i and i+1 (row i+1: sub, a[i+1], c1[i+1]) */
+            const double na = sub, nc1 = a[i + 1], nc2 = c1[i + 1];
+            const double oa = a[i], oc1 = c1[i], oc2 = c2[i];
+            a[i] = na; c1[i] = nc1; c2[i] = nc2;
+            const double tb = b[i]; b[i] = b[i + 1]; b[i + 1] = tb;
+            l[i] = oa / na;
+            a[i + 1] = oc1 - l[i] * c1[i];
+            c1[i + 1] = oc2 - l[i] * c2[i];
+        } else {
+            if (a[i] == 0.0) a[i] = tiny;
+            l[i] = sub / a[i];
+            a[i + 1] -= l[i] * c1[i];
+            c1[i + 1] -= l[i] * c2[i];
+        }
+        c2[i + 1] = 0.0;
+        b[i + 1] -= l[i] * b[i];
+    }
+    if (m > 0 && a[m - 1] == 0.0) a[m - 1] = tiny;
+    for (int32_t i = m - 1; i >= 0; --i) {        /* back substitution */
+        double s = b[i];
+        if (i + 1 < m) s -= c1[i] * b[i + 1];
+        if (i + 2 < m) s -= c2[i] * b[i + 2];
+        b[i] = s / a[i];
+    }
+}
+
+/* All eigenpairs of the symmetric m x m row-major M (destroyed): evals
+ * ascending, V row-major m x m with column i the unit eigenvector of
+ * evals[i].  Returns 0, or -1 on allocation failure. */
+int32_t oracle_sym_eigh(int32_t m, double* M, double* evals, double* V) {
+    if (m <= 0) return 0;
+    double* H = (double*)malloc(sizeof(double) * (size_t)m * m);
+    double* d = (double*)malloc(sizeof(double) * (size_t)m);
+    double* e = (double*)malloc(sizeof(double) * (size_t)m);
+    double* Y = (double*)malloc(sizeof(double) * (size_t)m * m);    /* column j at Y + j*m */
+    double* work = (double*)malloc(sizeof(double) * (size_t)m * 5 + sizeof(int32_t) * (size_t)m);
+    if (!H || !d || !e || !Y || !work) { free(H); free(d); free(e); free(Y); free(work); return -1; }
+    house_tridiag(m, M, H, d, e);
+    /* Gershgorin bounds of T */
+    double lo = d[0], hi = d[0], nrm = 0.0;
+    for (int32_t i = 0; i < m; ++i) {
+        const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+        if (d[i] - r < lo) lo = d[i] - r;
+        if (d[i] + r > hi) hi = d[i] + r;
+        if (fabs(d[i]) + r > nrm) nrm = fabs(d[i]) + r;
+    }
+    if (nrm == 0.0) nrm = 1.0;
+    const double eps = 2.220446049250313e-16, tiny = eps * nrm;
+    lo -= 2 * tiny;
+    hi += 2 * tiny;
+    /* eigenvalue r (ascending) = the x where the Sturm count passes r */
+    for (int32_t r = 0; r < m; ++r) {
+        double a = lo, b = hi;
+        for (int it = 0; it < 200 && b - a > 2 * eps * (fabs(a) + fabs(b)) + tiny * 1e-3; ++it) {
+            const double mid = 0.5 * (a + b);
+            if (sturm_below(m, d, e, mid, tiny * 1e-3) > r) b = mid;
+            else a = mid;
+        }
+        evals[r] = 0.5 * (a + b);
+    }
+    /* inverse iteration; a cluster = eigenvalues within 1e-3 * ||T|| of the previous one */
+    uint64_t seed = 0x9e3779b97f4a7c15ull;
+    int32_t c0 = 0;
+    for (int32_t r = 0; r < m; ++r) {
+        if (r > 0 && evals[r] - evals[r - 1] > 1e-3 * nrm) c0 = r;
+        double* y = Y + (size_t)r * m;
+        for (int32_t i = 0; i < m; ++i) {   /* a fixed pseudo-random start (xorshift) */
+            seed ^= seed << 13; seed ^= seed >> 7; seed ^= seed << 17;
+            y[i] = (double)(seed >> 11) / 9007199254740992.0 - 0.5;
+        }
+        for (int it = 0; it < 4; ++it) {
+            tridiag_solve(m, d, e, evals[r], tiny, y, work);
+            for (int32_t q = c0; q < r; ++q) {    /* orthogonal to the cluster's earlier vectors */
+                const double* z = Y + (size_t)q * m;
+                double dot = 0.0;
+                for (int32_t i = 0; i < m; ++i) dot += z[i] * y[i];
+                for (int32_t i = 0; i < m; ++i) y[i] -= dot * z[i];
+            }
+            double n2 = 0.0;
+            for (int32_t i = 0; i < m; ++i) n2 += y[i] * y[i];
+            n2 = sqrt(n2);
+            for (int32_t i = 0; i < m; ++i) y[i] /= n2;
+        }
+    }
+    /* eigenvectors of M: V[:, r] = H y_r */
+    for (int32_t i = 0; i < m; ++i)
+        for (int32_t r = 0; r < m; ++r) {
+            double s = 0.0;
+            for (int32_t j = 0; j < m; ++j) s += H[i * m + j] * Y[(size_t)r * m + j];
+            V[i * m + r] = s;
+        }
+    free(H); free(d); free(e); free(Y); free(work);
+    return 0;
+}
+
+/* Block Lanczos with full re-orthogonalisation.  op = 0: on the symmetric
+ * CSR matrix S (n_rows x n_rows); op = 1: on A^T A for the n_rows x n_cols
+ * CSR matrix A, applied as A q then A^T (A q) (its eigenvalues are the
+ * squared singular values of A; Section 5.5.2's SVD).  Q0 (n x b,
+ * row-major; n = n_rows for op 0, n_cols for op 1) is the start block.
+ * Builds an orthonormal Krylov basis of up to m_max columns, projects
+ * T = Q^T Op Q, diagonalises T with oracle_sym_eigh, and returns the nev
+ * largest Ritz values (descending) and their Ritz vectors (n x nev
+ * row-major).  Returns the basis size used, or -1 on allocation failure. */
+/* w = Op q for the operator of oracle_lanczos (t: n_rows scratch for op 1) */
+static void lanczos_op(int32_t op, int64_t n_rows, int64_t n_cols, const int64_t* row_ptr, const int32_t* col_idx,
+                       const void* val, int32_t vtype, const double* q, double* w, double* t) {
+    if (op == 0) {
+        for (int64_t i = 0; i < n_rows; ++i) {
+            double s = 0.0;
+            for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) s += vget(val, vtype, p) * q[col_idx[p]];
+            w[i] = s;
+        }
+        return;
+    }
+    for (int64_t i = 0; i < n_rows; ++i) {              /* t = A q */
+        double s = 0.0;
+        for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) s += vget(val, vtype, p) * q[col_idx[p]];
+        t[i] = s;
+    }
+    for (int64_t c = 0; c < n_cols; ++c) w[c] = 0.0;     /* w = A^T t, rows in order */
+    for (int64_t i = 0; i < n_rows; ++i)
+        for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) w[col_idx[p]] += vget(val, vtype, p) * t[i];
+}
+
+int32_t oracle_lanczos(int64_t n_rows, int64_t n_cols, const int64_t* row_ptr, const int32_t* col_idx,
+                       const void* val, int32_t vtype, int32_t op, int32_t b, int32_t m_max, const double* Q0,
+                       int32_t nev, double* evals, double* evecs) {
+    const int64_t n = op ? n_cols : n_rows;
     double* Q = (double*)calloc((size_t)n * m_max, sizeof(double));   /* column-major n x m */
     double* W = (double*)malloc(sizeof(double) * (size_t)n * b);
-    double* tmp = (double*)malloc(sizeof(double) * (size_t)n * b);
+    double* tmp = (double*)malloc(sizeof(double) * (size_t)(n_rows > n ? n_rows : n));
     if (!Q || !W || !tmp) { free(Q); free(W); free(tmp); return -1; }
     int32_t m = 0;
     /* orthonormalise a block of candidate columns against Q[:, :m] (twice)
@@ -313,32 +489,20 @@ int32_t oracle_lanczos(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
     while (m < m_max && m > done) {
         int32_t lo = done, hi = m;    /* expand the newest block */
         int32_t nb = hi - lo;
-        for (int32_t c = 0; c < nb; ++c) {
-            const double* q = Q + (size_t)(lo + c) * n;
-            double* w = W + (size_t)c * n;
-            for (int64_t i = 0; i < n; ++i) {
-                double s = 0.0;
-                for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
-                    s += vget(val, vtype, p) * q[col_idx[p]];
-                w[i] = s;
-            }
-        }
+        for (int32_t c = 0; c < nb; ++c)
+            lanczos_op(op, n_rows, n_cols, row_ptr, col_idx, val, vtype, Q + (size_t)(lo + c) * n,
+                       W + (size_t)c * n, tmp);
         done = hi;
         ORTH_APPEND(W, nb);
     }
     #undef ORTH_APPEND
-    /* T = Q^T S Q */
+    /* T = Q^T Op Q */
     double* T = (double*)calloc((size_t)m * m, sizeof(double));
     double* V = (double*)malloc(sizeof(double) * (size_t)m * m);
     double* ev = (double*)malloc(sizeof(double) * (size_t)m);
     double* Sq = (double*)malloc(sizeof(double) * (size_t)n);
     for (int32_t j = 0; j < m; ++j) {
-        const double* q = Q + (size_t)j * n;
-        for (int64_t i = 0; i < n; ++i) {
-            double s = 0.0;
-            for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) s += vget(val, vtype, p) * q[col_idx[p]];
-            Sq[i] = s;
-        }
+        lanczos_op(op, n_rows, n_cols, row_ptr, col_idx, val, vtype, Q + (size_t)j * n, Sq, tmp);
         for (int32_t r = 0; r < m; ++r) {
             const double* qr = Q + (size_t)r * n;
             double s = 0.0;
@@ -351,15 +515,10 @@ int32_t oracle_lanczos(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
             double a = 0.5 * (T[r * m + j] + T[j * m + r]);
             T[r * m + j] = a; T[j * m + r] = a;
         }
-    oracle_jacobi_eigh(m, T, ev, V);
-    /* pick the nev largest */
-    int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
-    for (int32_t i = 0; i < m; ++i) order[i] = i;
-    for (int32_t i = 0; i < m; ++i)
-        for (int32_t j = i + 1; j < m; ++j)
-            if (ev[order[j]] > ev[order[i]]) { int32_t t = order[i]; order[i] = order[j]; order[j] = t; }
-    for (int32_t e = 0; e < nev && e < m; ++e) {
-        int32_t c = order[e];
+    if (oracle_sym_eigh(m, T, ev, V) != 0) m = -1;
+    /* the nev largest: eigenvalues come ascending */
+    for (int32_t e = 0; m > 0 && e < nev && e < m; ++e) {
+        const int32_t c = m - 1 - e;
         evals[e] = ev[c];
         if (evecs)
             for (int64_t i = 0; i < n; ++i) {
@@ -368,7 +527,7 @@ int32_t oracle_lanczos(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
                 evecs[i * nev + e] = s;
             }
     }
-    free(order); free(T); free(V); free(ev); free(Sq);
+    free(T); free(V); free(ev); free(Sq);
     free(Q); free(W); free(tmp);
     return m;
 }

@@ -85,3 +85,24 @@ def test_svds_matches_dense_svd(sp):
     v = V.cpu().numpy()
     np.testing.assert_allclose(np.linalg.norm(D @ v, axis=0), sv, rtol=1e-5)     # ||A v|| = s
     h.close()
+
+
+def test_svds_matches_oracle(sp):
+    """Top singular values of a weighted directed R-MAT graph (Section 5.5.2's
+    SVD of a directed graph) against the FP64 oracle's Lanczos on A^T A, and
+    the right singular vectors' ||A v|| = s through the oracle's product."""
+    import torch
+    A = synth.rmat_csr(12, seed=6, weighted=True)
+    Q0 = synth.dense(A.n_cols, 8, seed=3).astype(np.float64)
+    ref, _, _ = oracle.svds(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.values, Q0, 6, 400)
+    h = sp.SparseMatrix.from_csr(A, transpose=True)
+    try:
+        V = torch.zeros((A.n_cols, 6), dtype=torch.float64, device="cuda")
+        sv, res, _ = h.svds(6, start_block(A.n_cols, 16), block=16, max_basis=64, max_restarts=400, tol=1e-6,
+                            right_vecs=V)
+        np.testing.assert_allclose(sv, ref, rtol=1e-6)
+        v = V.cpu().numpy()
+        Av = oracle.spmm(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.values, v)
+        np.testing.assert_allclose(np.linalg.norm(Av, axis=0), sv, rtol=1e-5)
+    finally:
+        h.close()

@@ -81,21 +81,60 @@ def test_16bit_x(sp, rmat16, rmat16_handles, xdtype, k, transpose):
     assert_close_rel(Y, ref, abs_product(A, Xr, transpose), 2e-3, f"{xdtype} k={k}")
 
 
+@pytest.fixture(scope="module")
+def rmat16_16bit_handles(sp, rmat16):
+    """Handles of the weighted scale-16 graph with bf16 and f16 stored values."""
+    import torch
+    out = {}
+    for vdtype in ("bfloat16", "float16"):
+        vt = torch.from_numpy(rmat16.values).to(getattr(torch, vdtype))
+        out[vdtype] = (sp.SparseMatrix(rmat16.n_rows, rmat16.n_cols, rmat16.row_ptr, rmat16.col_idx, vt,
+                                       transpose=True), vt.float().numpy().astype(np.float64))
+    yield out
+    for h, _ in out.values():
+        h.close()
+
+
 @pytest.mark.parametrize("vdtype", ["bfloat16", "float16"])
-def test_16bit_values(sp, rmat16, vdtype):
+@pytest.mark.parametrize("k", [1, 2, 8, 16, 64])
+def test_16bit_values(sp, rmat16, rmat16_16bit_handles, vdtype, k):
+    """Stored 16-bit values with X of the same type: every lane geometry (one
+    lane per row at k = 1, 2; two lanes at k = 8; lane groups at 16; two
+    column chunks of 16-bit lanes at 64), both orientations."""
     import torch
     A = rmat16
-    vt = torch.from_numpy(A.values).to(getattr(torch, vdtype))
-    h = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, vt, transpose=True)
-    Xd = to_dev(synth.dense(A.n_cols, 8, seed=4), getattr(torch, vdtype))
-    vr = vt.float().numpy().astype(np.float64)
+    h, vr = rmat16_16bit_handles[vdtype]
+    Xd = to_dev(synth.dense(A.n_cols, k, seed=4 + k), getattr(torch, vdtype))
     Xr = rounded_host(Xd)
     for tr in (False, True):
         Y = h.apply(Xd, transpose=tr).cpu().numpy()
         ref = oracle.spmm(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, vr, Xr, transpose=tr)
         scale = oracle.spmm(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, np.abs(vr), np.abs(Xr), transpose=tr)
-        assert_close_rel(Y, ref, scale, 2e-3, f"{vdtype} values t={tr}")
-    h.close()
+        assert_close_rel(Y, ref, scale, 2e-3, f"{vdtype} values k={k} t={tr}")
+
+
+@pytest.mark.parametrize("graph", ["sbm16_clustered", "sbm16_unclustered", "sbm1024_p90_clustered",
+                                   "rmat_permuted"])
+@pytest.mark.parametrize("k", [1, 4, 8, 32])
+def test_ordering_study_graphs_integer_exact(sp, graph, k):
+    """The ordering study's inputs (Section 5.1: SBM graphs with clustered or
+    randomly relabelled ids, R-MAT with relabelled ids) through the CUDA
+    path, pattern A with integer X, exactly the oracle's result."""
+    import torch
+    n = 1 << 15
+    A = {"sbm16_clustered": lambda: synth.sbm_csr(n, 16, 16, 0.5, seed=1),
+         "sbm16_unclustered": lambda: synth.sbm_csr(n, 16, 16, 0.5, seed=1, permuted=True),
+         "sbm1024_p90_clustered": lambda: synth.sbm_csr(n, 1024, 16, 0.9, seed=2),
+         "rmat_permuted": lambda: synth.rmat_permuted_csr(15, seed=3)}[graph]()
+    h = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, transpose=True)
+    try:
+        X = synth.dense(n, k, seed=k, mode="int")
+        for tr in (False, True):
+            got = h.apply(torch.from_numpy(X).cuda(), transpose=tr).cpu().numpy().astype(np.float64)
+            ref = oracle.spmm(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, X.astype(np.float64), transpose=tr)
+            assert np.array_equal(got, ref), (graph, k, tr)
+    finally:
+        h.close()
 
 
 def test_deterministic_repeat(sp, rmat16, rmat16_handles):

@@ -94,14 +94,68 @@ def test_nmf_objective_non_increasing():
 
 
 # ---------------------------------------------------------------- eigensolver
-def test_jacobi_vs_numpy_eigh():
+def test_sym_eigh_vs_numpy_eigh():
     rng = np.random.default_rng(0)
     M = rng.standard_normal((17, 17))
     M = M + M.T
-    ev, V = oracle.jacobi_eigh(M)
-    np.testing.assert_allclose(np.sort(ev), np.linalg.eigvalsh(M), rtol=1e-12, atol=1e-12)
+    ev, V = oracle.sym_eigh(M)
+    np.testing.assert_allclose(ev, np.linalg.eigvalsh(M), rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(M @ V, V * ev[None, :], atol=1e-11)
     np.testing.assert_allclose(V.T @ V, np.eye(17), atol=1e-12)
+
+
+def test_sym_eigh_repeated_and_clustered_eigenvalues():
+    """A multiple eigenvalue and a tight cluster: the vectors of each must
+    still be orthonormal eigenvectors (inverse iteration re-orthogonalises
+    within clusters)."""
+    rng = np.random.default_rng(1)
+    Q, _ = np.linalg.qr(rng.standard_normal((24, 24)))
+    lam = np.r_[np.full(5, 0.75), 0.5 + 1e-9 * np.arange(4), np.linspace(-1, 0.4, 15)]
+    M = (Q * lam[None, :]) @ Q.T
+    M = 0.5 * (M + M.T)
+    ev, V = oracle.sym_eigh(M)
+    np.testing.assert_allclose(ev, np.sort(lam), atol=1e-13)
+    np.testing.assert_allclose(M @ V, V * ev[None, :], atol=1e-12)
+    np.testing.assert_allclose(V.T @ V, np.eye(24), atol=1e-10)
+
+
+def test_sym_eigh_tridiagonal_and_diagonal_inputs():
+    # already tridiagonal (Householder leaves it), and diagonal with zeros off it
+    m = 30
+    d = np.linspace(-2, 3, m)
+    T = np.diag(d) + np.diag(np.full(m - 1, 0.3), 1) + np.diag(np.full(m - 1, 0.3), -1)
+    ev, V = oracle.sym_eigh(T)
+    np.testing.assert_allclose(ev, np.linalg.eigvalsh(T), atol=1e-13)
+    np.testing.assert_allclose(T @ V, V * ev[None, :], atol=1e-12)
+    D = np.diag(np.r_[3.0, -1.0, 2.0, 2.0, 0.0])
+    ev, V = oracle.sym_eigh(D)
+    np.testing.assert_allclose(ev, [-1.0, 0.0, 2.0, 2.0, 3.0], atol=1e-15)
+    np.testing.assert_allclose(np.abs(V.T @ V), np.eye(5), atol=1e-12)
+
+
+def test_svds_vs_numpy_svd():
+    """Singular values through Lanczos on A^T A (two products per step)."""
+    A = synth.rmat_csr(8, seed=4, weighted=True)
+    D = graphs.dense_of(A)
+    Q0 = synth.dense(A.n_cols, 6, seed=2).astype(np.float64)
+    sv, V, m = oracle.svds(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.values, Q0, 5, A.n_cols)
+    ref = np.linalg.svd(D, compute_uv=False)[:5]
+    np.testing.assert_allclose(sv, ref, rtol=1e-9)
+    np.testing.assert_allclose(np.linalg.norm(D @ V, axis=0), sv, rtol=1e-9)      # ||A v|| = s
+    np.testing.assert_allclose(V.T @ V, np.eye(5), atol=1e-9)
+
+
+def test_svds_rectangular_closed_form():
+    """A 3 x 5 matrix with orthogonal rows of norms 3, 2, 1: singular values
+    3, 2, 1 whatever the column count."""
+    rows = [[0, 1], [2], [3, 4]]
+    vals = [[3 / np.sqrt(2), 3 / np.sqrt(2)], [2.0], [0.6, 0.8]]
+    rp = np.r_[0, np.cumsum([len(r) for r in rows])].astype(np.int64)
+    ci = np.concatenate(rows).astype(np.int32)
+    va = np.concatenate(vals).astype(np.float64)
+    Q0 = synth.dense(5, 3, seed=1).astype(np.float64)
+    sv, _, _ = oracle.svds(3, 5, rp, ci, va, Q0, 3, 5)
+    np.testing.assert_allclose(sv, [3.0, 2.0, 1.0], atol=1e-12)
 
 
 def _normalised(A):

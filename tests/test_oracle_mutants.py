@@ -38,9 +38,18 @@ MUTANTS = {
     "nmf_w_numerator": ("W[i * k + r] *= AH[i * k + r] / (den[r] + eps);",
                         "W[i * k + r] *= AH[i * k + (r + 1) % k] / (den[r] + eps);",
                         [lambda: apps.test_nmf_vs_dense_updates(True)]),
-    # Jacobi rotation with the wrong sign on one side
-    "jacobi_sign": ("M[p * m + r] = c * mpr - s * mqr;", "M[p * m + r] = c * mpr + s * mqr;",
-                    [apps.test_jacobi_vs_numpy_eigh]),
+    # Householder update of the trailing block with a dropped rank-one term
+    "house_dropped_term": ("M[i * m + j] += -2.0 * v[i] * p[j] - 2.0 * p[i] * v[j] + 4.0 * vp * v[i] * v[j];",
+                           "M[i * m + j] += -2.0 * v[i] * p[j] - 2.0 * p[i] * v[j];",
+                           [apps.test_sym_eigh_vs_numpy_eigh]),
+    # Sturm count off by one comparison (counts eigenvalues at or above x)
+    "sturm_sign": ("if (q < 0.0) ++cnt;", "if (q > 0.0) ++cnt;", [apps.test_sym_eigh_vs_numpy_eigh]),
+    # no re-orthogonalisation inside clusters
+    "inverse_iteration_no_reorth": ("for (int32_t q = c0; q < r; ++q) {", "for (int32_t q = r; q < r; ++q) {",
+                                    [apps.test_sym_eigh_repeated_and_clustered_eigenvalues]),
+    # the A^T A operator applies A twice instead of A then A^T
+    "svd_operator": ("w[col_idx[p]] += vget(val, vtype, p) * t[i];", "w[i] += vget(val, vtype, p) * t[col_idx[p]];",
+                     [apps.test_svds_vs_numpy_svd]),
 }
 
 

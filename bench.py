@@ -656,6 +656,32 @@ def workload_nmf_batched(args):
     ms_p = event_ms(per_graph, args.steps)
     same = all(torch.equal(Yb[o:o + g.n_rows], y) for o, g, y in
                zip(np.cumsum([0] + [g.n_rows for g in graphs[:-1]]), graphs, Ys))
+    # spmm_apply_batched over the 256 separate handles: all k = 16, then k
+    # cycling over 1, 8, 33 (three kernel instantiations), against one
+    # spmm_apply per graph
+    hl = [s_.handle for s_ in singles]
+    Yq = [torch.empty_like(y) for y in Ys]
+    for _ in range(args.warmup):
+        spmm.spmm_apply_batched(hl, Xs, Yq)
+    ms_q = event_ms(lambda: spmm.spmm_apply_batched(hl, Xs, Yq), args.steps)
+    err_q = max(float(((a - b).abs() / (b.abs() + 1e-6)).max()) for a, b in zip(Yq, Ys))
+    kmix = [(1, 8, 33)[i % 3] for i in range(n_graphs)]
+    Xm = [torch.from_numpy(synth.dense(g.n_cols, kk, seed=i)).cuda() for i, (g, kk) in enumerate(zip(graphs, kmix))]
+    Ym = [torch.empty((g.n_rows, kk), device="cuda") for g, kk in zip(graphs, kmix)]
+    Ym1 = [torch.empty_like(y) for y in Ym]
+
+    def per_graph_mixed():
+        for s_, x, y in zip(singles, Xm, Ym1):
+            s_.apply(x, Y=y)
+    for _ in range(args.warmup):
+        spmm.spmm_apply_batched(hl, Xm, Ym)
+        per_graph_mixed()
+    ms_m = event_ms(lambda: spmm.spmm_apply_batched(hl, Xm, Ym), args.steps)
+    ms_m1 = event_ms(per_graph_mixed, args.steps)
+    nnz_m = sum(g.nnz for g in graphs)
+    apply_batched = {"k16_ms": ms_q, "k16_speedup_vs_per_graph": ms_p / ms_q, "k16_max_rel_diff": err_q,
+                     "mixed_k_1_8_33_ms": ms_m, "mixed_per_graph_ms": ms_m1,
+                     "mixed_speedup_vs_per_graph": ms_m1 / ms_m, "mixed_nnz_per_s": nnz_m / (ms_m / 1e3)}
     for s_ in singles:
         s_.close()
     nmf = {}
@@ -676,8 +702,9 @@ def workload_nmf_batched(args):
                                         float(np.median(obj[:, -1] / obj[:, 0])),
                                     "monotone_graphs": int(np.sum(np.all(np.diff(obj, axis=1)
                                                                          <= 1e-5 * obj[:, :-1], axis=1)))}
-            if kk == 16 and name == "f32":
-                # parity on the 4 smallest graphs against the FP64 oracle
+            if kk == 16:
+                # parity on the 4 smallest graphs against the FP64 oracle (FP32
+                # factors; BF16 factors: the error of the whole BF16 path)
                 offs_r = np.cumsum([0] + [g.n_rows for g in graphs])
                 offs_c = np.cumsum([0] + [g.n_cols for g in graphs])
                 w0, h0 = W0.cpu().numpy(), H0.cpu().numpy()
@@ -688,10 +715,16 @@ def workload_nmf_batched(args):
                                             w0[offs_r[i]:offs_r[i + 1]], h0[offs_c[i]:offs_c[i + 1]], steps)
                     worst = max(worst, float(np.max(np.abs(obj[i] - objr) / objr)))
                 nmf[f"k{kk}_{name}"]["oracle_objective_max_rel_err_4_smallest"] = worst
+                nmf[f"k{kk}_{name}"]["oracle_objective_final_rel_err_4_smallest"] = float(np.max(
+                    [abs(obj[i][-1] - oracle.nmf(graphs[i].n_rows, graphs[i].n_cols, graphs[i].row_ptr,
+                                                 graphs[i].col_idx, None, w0[offs_r[i]:offs_r[i + 1]],
+                                                 h0[offs_c[i]:offs_c[i + 1]], steps)[2][-1])
+                     / obj[i][-1] for i in np.argsort([g.n_rows for g in graphs])[:4]]))
     h.close()
     return base_line(args, "batched SpMM nonzeros/s (256 Chung-Lu graphs, one launch, k=16, FP32)",
                      nnz / (ms_b / 1e3), "nnz/s", ms_b, "chunglu256-batched-k16", "f32",
                      {"per_graph_launches_ms": ms_p, "batched_speedup": ms_p / ms_b, "bit_identical": same,
+                      "spmm_apply_batched": apply_batched,
                       "graphs": n_graphs, "vertices": nv, "nnz": nnz, "nmf_50_steps": nmf})
 
 

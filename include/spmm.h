@@ -277,6 +277,37 @@ int spmm_apply(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype x
                int64_t ldy, spmm_dtype ytype, int32_t transpose, void* stream);
 
 /*
+ * spmm_apply_batched -- Y_i = A_i X_i (or A_i^T X_i) for n handles, each with
+ * its own k_i, in one persistent launch per kernel instantiation the entries
+ * need (Section 3.4's single task queue over many multiplications): entries
+ * whose X rows share a vector width and chunking (for float32 X: k = 8, 12,
+ * ..., 64; k = 2, 4, 6, ...; k = 1 and odd k up to 31) run in one launch, their warp tasks
+ * numbered one after the other; the split rows of all entries are combined
+ * by one more launch.  Up to 128 entries share a launch; more make more
+ * launches.  The entries' arguments travel in the kernels' parameter space,
+ * so the call allocates nothing.
+ *   n        number of entries (>= 1)
+ *   A[i]     resident handles (not streaming, not SPMM_REORDER), all
+ *            different; with transpose, made with SPMM_WANT_TRANSPOSE
+ *   X[i]     device, row-major with ld = k[i] (contiguous), rows = n_cols
+ *            (A X) or n_rows (A^T X) of A[i], element type xtype
+ *   Y[i]     device float32, row-major with ld = k[i], rows = n_rows (A X)
+ *            or n_cols (A^T X) of A[i]; overwritten
+ *   k[i]     1..64
+ *   xtype    F32, BF16 or F16 for every entry
+ * Each Y_i equals spmm_apply on its own handle within the tolerances of
+ * spmm_apply (the same sums; short rows are always walked whole per lane
+ * group and the shared-memory hot rows are not used, so rows on several
+ * lanes may be added in another order).  Asynchronous on `stream`; calls
+ * that share a handle must not overlap.
+ * Errors: SPMM_ERR_ARG (NULL, k, repeated handle, transpose without
+ * SPMM_WANT_TRANSPOSE), SPMM_ERR_UNSUPPORTED (streaming or relabelled handle,
+ * 16-bit values with another X type), SPMM_ERR_CUDA.
+ */
+int spmm_apply_batched(int32_t n, const spmm_mat_t* A, const void* const* X, void* const* Y, const int32_t* k,
+                       spmm_dtype xtype, int32_t transpose, void* stream);
+
+/*
  * spmm_sync_status -- synchronise `stream` and report whether any call on A
  * since the last check hit a device-side timeout.  The kernels stage the
  * matrix with asynchronous copies and wait for them with a bound (2 s); a

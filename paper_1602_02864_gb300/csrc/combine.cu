@@ -11,13 +11,9 @@ namespace spmm {
 // segments g, g + SG, ... in order, then the groups' sums are added by a
 // fixed xor-shuffle tree, so the result is the same on every run.
 // Compensated partials are added in segment order by one group (SG = 1).
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-combine_kernel(const int4* __restrict__ splits, int64_t n_splits, const float* __restrict__ partials,
-               float* __restrict__ Y, int64_t ldy, int32_t k, int32_t lanes_log2, const float* __restrict__ pcomp) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + w;
-    if (s >= n_splits) return;                 // whole warps
-    const int4 sp = splits[s];                 // {row, nseg, slot0, 0}
+__device__ __forceinline__ void combine_row(const int4 sp, const float* __restrict__ partials, float* __restrict__ Y,
+                                            int64_t ldy, int32_t k, int32_t lanes_log2,
+                                            const float* __restrict__ pcomp, int lane) {
     if (pcomp) {                               // Neumaier summation of (sum, compensation) partials
         for (int c = lane; c < k; c += 32) {
             const int64_t base = (int64_t)sp.z * k + c;
@@ -55,11 +51,53 @@ combine_kernel(const int4* __restrict__ splits, int64_t n_splits, const float* _
     }
 }
 
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+combine_kernel(const int4* __restrict__ splits, int64_t n_splits, const float* __restrict__ partials,
+               float* __restrict__ Y, int64_t ldy, int32_t k, int32_t lanes_log2, const float* __restrict__ pcomp) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+    if (s >= n_splits) return;                 // whole warps
+    combine_row(splits[s], partials, Y, ldy, k, lanes_log2, pcomp, lane);
+}
+
+// the split rows of several matrices (spmm_apply_batched): warp s takes split
+// row s of the concatenated lists, entry e owning rows off[e] .. off[e+1]-1
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) combine_multi_kernel(const __grid_constant__ CombineMulti m) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + w;
+    if (s >= m.off[m.n]) return;
+    int lo = 0, hi = m.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (m.off[mid] <= s) lo = mid;
+        else hi = mid - 1;
+    }
+    const CombineEntry& E = m.ent[lo];
+    combine_row(E.splits[s - m.off[lo]], E.partials, E.Y, E.ldy, E.k, E.lanes_log2, E.pcomp, lane);
+}
+
+static int combine_lanes_log2(int32_t k) {
+    int lg = 0;
+    while ((1 << lg) < k && lg < 5) ++lg;
+    return lg;
+}
+
+cudaError_t launch_combine_multi(CombineMulti& m, cudaStream_t s) {
+    m.off[0] = 0;
+    for (int e = 0; e < m.n; ++e) {
+        m.ent[e].lanes_log2 = combine_lanes_log2(m.ent[e].k);
+        m.off[e + 1] = m.off[e] + m.ent[e].n_splits;
+    }
+    if (m.off[m.n] <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((m.off[m.n] + kWarpsPerBlock - 1) / kWarpsPerBlock));
+    combine_multi_kernel<<<grid, kWarpsPerBlock * 32, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_combine(const int4* splits, int64_t n_splits, const float* partials, float* Y,
                            int64_t ldy, int32_t k, cudaStream_t s, const float* partials_comp) {
     if (n_splits <= 0) return cudaSuccess;
-    int lg = 0;
-    while ((1 << lg) < k && lg < 5) ++lg;
+    const int lg = combine_lanes_log2(k);
     const dim3 block(kWarpsPerBlock * 32);
     const dim3 grid((unsigned)((n_splits + kWarpsPerBlock - 1) / kWarpsPerBlock));
     combine_kernel<<<grid, block, 0, s>>>(splits, n_splits, partials, Y, ldy, k, lg, partials_comp);

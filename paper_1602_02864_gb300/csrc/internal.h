@@ -311,6 +311,20 @@ struct FwdArgs {
     int64_t hot_bytes = 0;
 };
 
+// One launch over the tasks of several matrices (spmm_apply_batched): the
+// entries' arguments travel in the kernel's parameter space (no device
+// allocation); the tasks of entry e are numbers off[e] .. off[e+1]-1 of the
+// launch.  g holds the launch-wide fields: n_tasks (all entries), task_ctr,
+// task_chunk, status, wait_ns.
+constexpr int kMaxBatch = 128;
+struct MultiArgs {
+    FwdArgs g;
+    int32_t n;
+    int64_t off[kMaxBatch + 1];
+    FwdArgs ent[kMaxBatch];
+};
+static_assert(sizeof(MultiArgs) <= 32000, "kernel parameter space holds at most 32764 bytes");
+
 // Launches from a handle are scheduled dynamically.  Tasks over wide X rows
 // (at least kWideRowBytes bytes) vary a lot in time (gathers that miss L2)
 // and are claimed one at a time (R-MAT scale 24, FP32: k = 4 1.95 -> 1.92 ms,
@@ -344,6 +358,30 @@ cudaError_t launch_rows_f16_mg(const FwdArgs& a, int vmode, int vec, int ch, cud
 cudaError_t launch_rows_f32_hot(const FwdArgs& a, int vmode, int vec, cudaStream_t s);
 cudaError_t launch_rows_bf16_hot(const FwdArgs& a, int vmode, int vec, cudaStream_t s);
 cudaError_t launch_rows_f16_hot(const FwdArgs& a, int vmode, int vec, cudaStream_t s);
+
+// rows_multi_*.cu: one launch of the generic task kernel over the entries of
+// M (same X type, value mode, vector width, chunks and compensation)
+cudaError_t launch_rows_multi_f32(const MultiArgs& M, int vmode, int vec, int ch, bool comp, cudaStream_t s);
+cudaError_t launch_rows_multi_bf16(const MultiArgs& M, int vmode, int vec, int ch, bool comp, cudaStream_t s);
+cudaError_t launch_rows_multi_f16(const MultiArgs& M, int vmode, int vec, int ch, bool comp, cudaStream_t s);
+
+// combine.cu: the split rows of several matrices in one launch
+// (spmm_apply_batched); launch_combine_multi fills off[] and lanes_log2
+struct CombineEntry {
+    const int4* splits;
+    int64_t n_splits;
+    const float* partials;
+    const float* pcomp;     // compensation terms, or null
+    float* Y;
+    int64_t ldy;
+    int32_t k, lanes_log2;
+};
+struct CombineMulti {
+    int32_t n;
+    int64_t off[kMaxBatch + 1];
+    CombineEntry ent[kMaxBatch];
+};
+cudaError_t launch_combine_multi(CombineMulti& m, cudaStream_t s);
 
 // combine.cu: Y[row] = sum of the split row's partials in a fixed order.
 cudaError_t launch_combine(const int4* splits, int64_t n_splits, const float* partials, float* Y,

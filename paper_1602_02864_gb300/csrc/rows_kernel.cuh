@@ -335,9 +335,13 @@ constexpr int warps_per_block() {
 // names row ~c of the hot rows of X, which the block copies into shared
 // memory (after its warps' staging buffers) before its first task, so those
 // gathers leave the L1-to-L2 request path alone (hot.cu).
-template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, int MG = 0, bool HOT = false>
-__global__ void __launch_bounds__(warps_per_block<HOT>() * 32, (HOT ? 1 : min_blocks<VMODE, MG>()))
-    rows_kernel(FwdArgs a) {
+// MULTI: the tasks of several matrices (MultiArgs M, spmm_apply_batched),
+// numbered one after the other; every task takes the matrix, X, Y, k and
+// lane geometry of its own entry.  ga holds the launch-wide fields (task
+// count, counter, status, wait bound).
+template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, int MG, bool HOT, bool MULTI>
+__device__ __forceinline__ void rows_run(const FwdArgs& ga, const MultiArgs* M) {
+    static_assert(!MULTI || (!ONE && MG == 0 && !HOT), "batched launches use the generic row walk");
     static_assert(!ONE || CH == 1, "one lane per row needs CH == 1");
     static_assert(MG == 0 || (!ONE && CH == 1), "merge over lane groups needs several lanes and CH == 1");
     static_assert(!HOT || (ONE && MG == 0 && VEC * sizeof(XT) <= 4), "hot rows in shared memory: <= 4-byte rows");
@@ -368,6 +372,7 @@ __global__ void __launch_bounds__(warps_per_block<HOT>() * 32, (HOT ? 1 : min_bl
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* wb = smem + w * Lay::kWarp;
     uint64_t* bars = reinterpret_cast<uint64_t*>(wb + 2 * Lay::kBuf);
+    const FwdArgs& a = ga;      // launch-wide fields (and, unless MULTI, the matrix's)
     const XT* hs = nullptr;     // hot rows of X in shared memory (HOT)
     if constexpr (HOT) {
         // one bulk copy of the packed hot rows, before any warp leaves
@@ -400,17 +405,50 @@ __global__ void __launch_bounds__(warps_per_block<HOT>() * 32, (HOT ? 1 : min_bl
     }
     __syncwarp();
 
-    // lane geometry
-    const int lg = ONE ? 0 : a.lanes_log2;
-    const int LANES = 1 << lg, G = 32 >> lg;
-    const int g = lane >> lg, li = lane & (LANES - 1);
-    bool act[CH];
-#pragma unroll
-    for (int c = 0; c < CH; ++c) act[c] = (li + c * LANES) < a.nvec;
-    const XT* xb = reinterpret_cast<const XT*>(a.X) + (int64_t)li * VEC;
+    // the entry of task t (MULTI: a binary search of the entries' first tasks)
+    // and its two descriptors
+    auto fetch = [&](int64_t tt, int4& x0, int4& x1) -> int {
+        if constexpr (MULTI) {
+            int lo = 0, hi = M->n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (M->off[mid] <= tt) lo = mid;
+                else hi = mid - 1;
+            }
+            const int64_t tl = tt - M->off[lo];
+            x0 = M->ent[lo].tasks[tl];
+            x1 = M->ent[lo].tasks[tl + 1];
+            return lo;
+        } else {
+            x0 = a.tasks[tt];
+            x1 = a.tasks[tt + 1];
+            return 0;
+        }
+    };
+    auto entry = [&](int e) -> const FwdArgs& {
+        if constexpr (MULTI) return M->ent[e];
+        else return a;
+    };
 
+    // lane geometry (of the current task's entry when MULTI)
+    int lg = 0, LANES = 1, G = 32, g = 0, li = 0;
+    bool act[CH];
+    const XT* xb = nullptr;
     const uint64_t apol = policy_evict_first();
-    const uint64_t xpol = a.x_evict_last ? policy_evict_last() : policy_evict_normal();
+    uint64_t xpol = 0;
+    const FwdArgs* cur = &a;    // the entry of the task being computed
+    auto set_geometry = [&](const FwdArgs& E) {
+        lg = ONE ? 0 : E.lanes_log2;
+        LANES = 1 << lg;
+        G = 32 >> lg;
+        g = lane >> lg;
+        li = lane & (LANES - 1);
+#pragma unroll
+        for (int c = 0; c < CH; ++c) act[c] = (li + c * LANES) < E.nvec;
+        xb = reinterpret_cast<const XT*>(E.X) + (int64_t)li * VEC;
+        xpol = E.x_evict_last ? policy_evict_last() : policy_evict_normal();
+        cur = &E;
+    };
     // load the X row of column index c (elements off.. of this lane's part)
     auto gather = [&](auto& xv, int64_t c, int off) {
         if constexpr (HOT) {
@@ -419,10 +457,12 @@ __global__ void __launch_bounds__(warps_per_block<HOT>() * 32, (HOT ? 1 : min_bl
                 return;
             }
         }
-        xv.load(xb + c * a.ldx + off, xpol);
+        xv.load(xb + c * cur->ldx + off, xpol);
     };
-    int4 d0 = a.tasks[t], d1 = a.tasks[t + 1];
-    if (lane == 0) issue_task<VMODE>(a, d0, d1, wb, &bars[0], apol);
+    int4 d0, d1;
+    int ed = fetch(t, d0, d1);
+    set_geometry(entry(ed));
+    if (lane == 0) issue_task<VMODE>(entry(ed), d0, d1, wb, &bars[0], apol);
     // the next task: static stride, or the next of a chunk claimed from the
     // counter by lane 0
     int64_t cnext = 0, cend = 0;
@@ -437,7 +477,8 @@ __global__ void __launch_bounds__(warps_per_block<HOT>() * 32, (HOT ? 1 : min_bl
     };
     int64_t tn = next_task(t);
     int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
-    if (tn < a.n_tasks) { n0 = a.tasks[tn]; n1 = a.tasks[tn + 1]; }
+    int en = 0;
+    if (tn < a.n_tasks) en = fetch(tn, n0, n1);
     uint32_t phase = 0;     // bit b = parity to wait for on buffer b
     int b = 0;
 
@@ -447,13 +488,14 @@ __global__ void __launch_bounds__(warps_per_block<HOT>() * 32, (HOT ? 1 : min_bl
             __syncwarp();
             if (lane == 0) {
                 fence_proxy_async();
-                issue_task<VMODE>(a, n0, n1, wb + (b ^ 1) * Lay::kBuf, &bars[b ^ 1], apol);
+                issue_task<VMODE>(entry(en), n0, n1, wb + (b ^ 1) * Lay::kBuf, &bars[b ^ 1], apol);
             }
         }
         // prefetch the descriptor after next
         const int64_t tnn = tn < a.n_tasks ? next_task(tn) : a.n_tasks;
         int4 m0 = make_int4(0, 0, 0, 0), m1 = m0;
-        if (tnn < a.n_tasks) { m0 = a.tasks[tnn]; m1 = a.tasks[tnn + 1]; }
+        int em = 0;
+        if (tnn < a.n_tasks) em = fetch(tnn, m0, m1);
 
         if (!mbar_wait_bounded(&bars[b], (phase >> b) & 1u, a.wait_ns)) {
             if (lane == 0) atomicOr(a.status, kStatusTimeout);
@@ -463,7 +505,11 @@ __global__ void __launch_bounds__(warps_per_block<HOT>() * 32, (HOT ? 1 : min_bl
         phase ^= 1u << b;
 
         // ---- compute task (d0, d1) from buffer b
+        if constexpr (MULTI) {
+            if (cur != &entry(ed)) set_geometry(entry(ed));
+        }
         {
+            const FwdArgs& a = *cur;   // the task's entry (the launch's matrix unless MULTI)
             const unsigned char* buf = wb + b * Lay::kBuf;
             const int64_t e0 = desc_e0(d0);
             const int n = (int)(desc_e0(d1) - e0);
@@ -876,11 +922,24 @@ __global__ void __launch_bounds__(warps_per_block<HOT>() * 32, (HOT ? 1 : min_bl
             }
         }
         if (tn >= a.n_tasks) break;
-        d0 = n0; d1 = n1;
-        n0 = m0; n1 = m1;
+        d0 = n0; d1 = n1; ed = en;
+        n0 = m0; n1 = m1; en = em;
         tn = tnn;
         b ^= 1;
     }
+}
+
+template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, int MG = 0, bool HOT = false>
+__global__ void __launch_bounds__(warps_per_block<HOT>() * 32, (HOT ? 1 : min_blocks<VMODE, MG>()))
+    rows_kernel(const __grid_constant__ FwdArgs a) {
+    rows_run<XT, VMODE, VEC, CH, COMP, ONE, MG, HOT, false>(a, nullptr);
+}
+
+// the tasks of up to kMaxBatch matrices in one launch (spmm_apply_batched);
+// two blocks per SM, so the per-task lane geometry fits in registers
+template <typename XT, int VMODE, int VEC, int CH, bool COMP>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) rows_kernel_multi(const __grid_constant__ MultiArgs m) {
+    rows_run<XT, VMODE, VEC, CH, COMP, false, 0, false, true>(m.g, &m);
 }
 
 template <typename XT, int VMODE, int VEC, int CH, bool COMP, bool ONE, int MG = 0, bool HOT = false>
@@ -923,6 +982,58 @@ cudaError_t launch_one(const FwdArgs& a, cudaStream_t s) {
     const dim3 grid((unsigned)(want < cap ? want : cap));
     rows_kernel<XT, VMODE, VEC, CH, COMP, ONE, MG, HOT><<<grid, WPB * 32, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// One launch over the entries of M (generic row walk, three blocks per SM).
+template <typename XT, int VMODE, int VEC, int CH, bool COMP>
+cudaError_t launch_multi_one(const MultiArgs& m, cudaStream_t s) {
+    using Lay = Layout<VMODE>;
+    static std::once_flag once;
+    static int blocks_per_sm = 0, num_sms = 0;
+    static cudaError_t setup = cudaSuccess;
+    std::call_once(once, [] {
+        cudaError_t e = cudaSuccess;
+        int dev = 0, nb = 0, sms = 0;
+        if (Lay::kBlock > 48 * 1024)
+            e = cudaFuncSetAttribute(rows_kernel_multi<XT, VMODE, VEC, CH, COMP>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::kBlock);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rows_kernel_multi<XT, VMODE, VEC, CH, COMP>,
+                                                              kWarpsPerBlock * 32, Lay::kBlock);
+        setup = e;
+        num_sms = sms;
+        blocks_per_sm = nb > 0 ? nb : 1;
+    });
+    if (setup != cudaSuccess) return setup;
+    const int64_t want = (m.g.n_tasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int64_t cap = (int64_t)blocks_per_sm * num_sms;
+    const dim3 grid((unsigned)(want < cap ? want : cap));
+    rows_kernel_multi<XT, VMODE, VEC, CH, COMP><<<grid, kWarpsPerBlock * 32, Lay::kBlock, s>>>(m);
+    return cudaGetLastError();
+}
+
+template <typename XT>
+cudaError_t launch_rows_multi_t(const MultiArgs& m, int vmode, int vec, int ch, bool comp, cudaStream_t s) {
+    if (m.g.n_tasks <= 0) return cudaSuccess;
+#define SPMM_LAUNCH_MULTI(VM, V, C)                                                      \
+    if (vmode == VM && vec == V && ch == C)                                              \
+        return comp ? launch_multi_one<XT, VM, V, C, true>(m, s) : launch_multi_one<XT, VM, V, C, false>(m, s);
+    if constexpr (sizeof(XT) == 4) {
+        SPMM_LAUNCH_MULTI(0, 4, 1) SPMM_LAUNCH_MULTI(0, 2, 1) SPMM_LAUNCH_MULTI(0, 1, 1) SPMM_LAUNCH_MULTI(0, 1, 2)
+        SPMM_LAUNCH_MULTI(1, 4, 1) SPMM_LAUNCH_MULTI(1, 2, 1) SPMM_LAUNCH_MULTI(1, 1, 1) SPMM_LAUNCH_MULTI(1, 1, 2)
+    } else {
+        constexpr int VM3 = std::is_same<XT, __half>::value ? 3 : 2;
+        SPMM_LAUNCH_MULTI(0, 8, 1) SPMM_LAUNCH_MULTI(0, 4, 1) SPMM_LAUNCH_MULTI(0, 2, 1) SPMM_LAUNCH_MULTI(0, 1, 1)
+        SPMM_LAUNCH_MULTI(0, 1, 2)
+        SPMM_LAUNCH_MULTI(1, 8, 1) SPMM_LAUNCH_MULTI(1, 4, 1) SPMM_LAUNCH_MULTI(1, 2, 1) SPMM_LAUNCH_MULTI(1, 1, 1)
+        SPMM_LAUNCH_MULTI(1, 1, 2)
+        SPMM_LAUNCH_MULTI(VM3, 8, 1) SPMM_LAUNCH_MULTI(VM3, 4, 1) SPMM_LAUNCH_MULTI(VM3, 2, 1)
+        SPMM_LAUNCH_MULTI(VM3, 1, 1) SPMM_LAUNCH_MULTI(VM3, 1, 2)
+    }
+#undef SPMM_LAUNCH_MULTI
+    return cudaErrorInvalidValue;
 }
 
 // One lane per X row of at most 4 bytes, hot rows in shared memory.

@@ -86,6 +86,8 @@ _lib.spmm_plan_walk_eff.restype = ctypes.c_int
 _lib.spmm_apply_csr_static.argtypes = [_i64, _i64, _i64, _P, _P, _P, ctypes.c_int, _P, _i64, _i64, _P, _i64,
                                        _i32, ctypes.c_int, _P, _i64, _P]
 _lib.spmm_apply_csr_static.restype = ctypes.c_int
+_lib.spmm_apply_batched.argtypes = [_i32, _P, _P, _P, _P, ctypes.c_int, _i32, _P]
+_lib.spmm_apply_batched.restype = ctypes.c_int
 _lib.spmm_static_status.argtypes = [_P]
 _lib.spmm_static_status.restype = ctypes.c_int
 _lib.spmm_pagerank.argtypes = [_P, ctypes.c_double, _i32, _P, _P, _P, _P]
@@ -195,6 +197,24 @@ def spmm_create_csr(n_rows, n_cols, row_ptr, col_idx, values=None, flags=0, opts
 def spmm_apply(h, X, ldx, k, xtype, Y, ldy, transpose=0, stream=None):
     _check(_lib.spmm_apply(h, _ptr(X), int(ldx), int(k), int(xtype), _ptr(Y), int(ldy), SPMM_F32,
                            int(transpose), _stream_handle(stream)))
+
+
+def spmm_apply_batched(handles, Xs, Ys, transpose=False, stream=None):
+    """Y_i = A_i X_i (or A_i^T X_i) for lists of handles, contiguous CUDA
+    tensors X_i (one dtype) and float32 CUDA tensors Y_i (see spmm.h)."""
+    n = len(handles)
+    if len(Xs) != n or len(Ys) != n or n == 0:
+        raise ValueError("need as many X and Y tensors as handles (at least one)")
+    xtype = _torch_dtype_code(Xs[0])
+    for X, Y in zip(Xs, Ys):
+        if _torch_dtype_code(X) != xtype or not X.is_contiguous() or not Y.is_contiguous() \
+                or X.shape[1] != Y.shape[1]:
+            raise ValueError("X tensors of one dtype, X and Y contiguous with equal columns")
+    hs = (_P * n)(*[h.value if isinstance(h, _P) else h for h in handles])
+    xs = (_P * n)(*[X.data_ptr() for X in Xs])
+    ys = (_P * n)(*[Y.data_ptr() for Y in Ys])
+    ks = (_i32 * n)(*[int(X.shape[1]) for X in Xs])
+    _check(_lib.spmm_apply_batched(n, hs, xs, ys, ks, xtype, int(bool(transpose)), _stream_handle(stream)))
 
 
 def spmm_sync_status(h, stream=None):

@@ -599,6 +599,43 @@ int spmm_eigs(spmm_mat_t S, int32_t nev, int32_t block, int32_t max_basis, int32
               int32_t* restarts_out, void* stream);
 
 /*
+ * spmm_eigs_filtered -- the nev largest eigenpairs of a symmetric S by
+ * Chebyshev-filtered subspace iteration: a block of `block` vectors is
+ * multiplied by the degree-`degree` Chebyshev polynomial that stays within
+ * [-1, 1] on [lower, cut] (cut = the block's smallest Ritz value) and grows
+ * fastest above it, through `degree` block SpMMs (X in FP32 or BF16, FP32
+ * accumulation, the three-term recurrence in FP32 scaled to stay O(1)), then
+ * orthonormalised (CholQR2) and Rayleigh-Ritz projected with S in FP64.  Not
+ * the paper's Krylov-Schur solver (spmm_eigs): the same products (Section 4.2's
+ * only sparse operation is the block SpMM), arranged so that the FP64 work is
+ * once per `degree` SpMMs, which converges on the clustered top spectrum of a
+ * large normalised graph where the restarted Krylov method does not within
+ * its restarts.  The filter steps of one iteration run as one CUDA graph.
+ *   S            square handle of a symmetric matrix (values F32, BF16 or none)
+ *   nev          eigenpairs wanted
+ *   block        vectors filtered together, nev + 1 <= block <= min(64, n)
+ *                (a few more than nev: the filter separates the wanted
+ *                eigenvalues from the block's smallest Ritz value)
+ *   degree       polynomial degree per iteration, 1..1000
+ *   lower        a lower bound of S's spectrum (-1 for a normalised
+ *                adjacency matrix D^-1/2 A D^-1/2)
+ *   max_iters    filter iterations before giving up (best pairs returned)
+ *   xtype        SPMM_F32 or SPMM_BF16: type of the block fed to the filter's
+ *                SpMMs; the Rayleigh-Ritz product reads FP32 (BF16 with BF16
+ *                values)
+ *   tol, V0 (n x block), evals, evecs, resid   as for spmm_eigs
+ *   iters_out    host int32 iterations used, or NULL
+ * Synchronises `stream`; runs on an internal stream; allocates its workspace
+ * (about 6 * n * block doubles and 4 * n * block floats).  Errors:
+ * SPMM_ERR_ARG (sizes, NULL, rank-deficient start block, Ritz values not
+ * above `lower`, a filtered block that lost rank), SPMM_ERR_UNSUPPORTED,
+ * SPMM_ERR_TIMEOUT, SPMM_ERR_OOM, SPMM_ERR_CUDA.
+ */
+int spmm_eigs_filtered(spmm_mat_t S, int32_t nev, int32_t block, int32_t degree, double lower, int32_t max_iters,
+                       double tol, spmm_dtype xtype, const double* V0, double* evals, double* evecs, double* resid,
+                       int32_t* iters_out, void* stream);
+
+/*
  * spmm_replan -- rebuild the warp-task plan of one orientation of a resident
  * handle for new tuning knobs (the matrix itself is not copied again).  The
  * paper sizes its tile-row batches from the cache size and the number of

@@ -121,6 +121,23 @@ __global__ void residual_kernel(const double* __restrict__ AU, const double* __r
         R[t] = AU[t] - theta[t % q] * U[t];
 }
 
+// Chebyshev filter step (FP32): Yn = alpha * SY + beta * Yc + gamma * Yp,
+// coefficients (alpha, beta, gamma) read from device memory so one captured
+// graph serves every filter interval
+__global__ void cheb_step_kernel(const float* __restrict__ SY, const float* __restrict__ Yc,
+                                 const float* __restrict__ Yp, float* __restrict__ Yn, int64_t total,
+                                 const float* __restrict__ coef) {
+    const float al = coef[0], be = coef[1], ga = coef[2];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+        Yn[t] = fmaf(al, SY[t], fmaf(be, Yc[t], Yp ? ga * Yp[t] : 0.f));
+}
+
+// contiguous FP32 -> BF16 (the SpMM input of a BF16 filter step)
+__global__ void f32_to_bf16_kernel(const float* __restrict__ src, int64_t total, __nv_bfloat16* __restrict__ dst) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = __float2bfloat16(src[t]);
+}
+
 // ---------------------------------------------------------------- host linear algebra
 // Cholesky G = R^T R (R upper); false if a pivot is not safely positive.
 static bool cholesky_upper(int b, const std::vector<double>& G, std::vector<double>& R) {
@@ -432,4 +449,234 @@ extern "C" int spmm_svds(spmm_mat_t A, int32_t nsv, int32_t block, int32_t max_b
     if (rc == SPMM_OK)
         for (int i = 0; i < nsv; ++i) svals[i] = std::sqrt(std::max(0.0, svals[i]));
     return rc;
+}
+
+// ---------------------------------------------------------------- filtered subspace iteration
+// The block of s vectors U is multiplied by the Chebyshev polynomial of degree
+// d that is bounded by 1 on [lower, cut] and grows fastest above it (cut = the
+// smallest Ritz value of the block, so every wanted direction is amplified
+// against the rest), in FP32 through d block SpMMs; the filtered block is then
+// orthonormalised (CholQR2) and Rayleigh-Ritz projected with S (one more SpMM)
+// in FP64.  The three-term recurrence is scaled to stay O(1) at the largest
+// Ritz value (Zhou and Saad's scaled Chebyshev filter):
+//   e = (cut - lower) / 2, c = (cut + lower) / 2, s1 = e / (top - c)
+//   Y1 = (s1 / e) (S - c) Y0
+//   Y{j+1} = (2 s{j+1} / e) (S - c) Yj - sj s{j+1} Y{j-1},  s{j+1} = 1 / (2 / s1 - sj)
+// The d filter steps run as one CUDA graph, captured on the first iteration
+// and relaunched with new coefficients.
+static int eigs_filtered_impl(spmm_mat_t S, int32_t nev, int32_t block, int32_t degree, double lower,
+                              int32_t max_iters, double tol, spmm_dtype xtype, const double* V0, double* evals,
+                              double* evecs, double* resid, int32_t* iters_out, void* stream) {
+    if (!S || !V0 || !evals) { set_error("spmm_eigs_filtered: NULL argument"); return SPMM_ERR_ARG; }
+    NvtxRange range("spmm_eigs_filtered");
+    const int64_t n = S->fwd.n_rows;
+    if (S->fwd.n_cols != n || n < 1) { set_error("spmm_eigs_filtered: the matrix must be square"); return SPMM_ERR_ARG; }
+    if (nev < 1 || block < nev + 1 || block > kEigMaxBasis || block > n || degree < 1 || degree > 1000 ||
+        max_iters < 0 || !(tol > 0.0) || !std::isfinite(lower)) {
+        set_error("spmm_eigs_filtered: need nev + 1 <= block <= min(64, n), 1 <= degree <= 1000, max_iters >= 0, "
+                  "tol > 0, a finite lower bound");
+        return SPMM_ERR_ARG;
+    }
+    if (xtype != SPMM_F32 && xtype != SPMM_BF16) { set_error("spmm_eigs_filtered: xtype must be F32 or BF16"); return SPMM_ERR_ARG; }
+    if (S->vtype == SPMM_F16 || (S->vtype == SPMM_BF16 && xtype != SPMM_BF16)) {
+        set_error("spmm_eigs_filtered: 16-bit values need X of the same type (use F32 values)");
+        return SPMM_ERR_UNSUPPORTED;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int b = block;
+    Eig E;
+    E.A = S;
+    E.n = n;
+    E.m = b;
+    E.b = b;
+    // the Rayleigh-Ritz product S U reads U in FP32 (xtype is the filter's
+    // SpMM input): with BF16 there, the residuals could not fall below BF16's
+    // rounding of U
+    E.xtype = S->vtype == SPMM_BF16 ? SPMM_BF16 : SPMM_F32;
+    E.grid = std::max(1, sms * 8);
+    E.chunk = std::max<int64_t>(1024, (n + 1023) / 1024);
+    E.nchunks = (int)((n + E.chunk - 1) / E.chunk);
+    float* Yc[3] = {nullptr, nullptr, nullptr};
+    float* coef = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = SPMM_OK;
+    cudaError_t e = cudaSuccess;
+    auto fail = [&](cudaError_t err, const char* what) { rc = cuda_fail(err, what); };
+    const int64_t nb = n * b;
+    do {
+        if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess) { fail(e, "spmm_eigs_filtered: stream"); break; }
+        if ((e = cudaStreamCreateWithFlags(&E.s, cudaStreamNonBlocking)) != cudaSuccess) { fail(e, "spmm_eigs_filtered: stream"); break; }
+        const size_t nm = (size_t)nb * sizeof(double);
+        if ((e = cudaMalloc((void**)&E.V, nm)) != cudaSuccess || (e = cudaMalloc((void**)&E.AV, nm)) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.U, nm)) != cudaSuccess || (e = cudaMalloc((void**)&E.AU, nm)) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.W, nm)) != cudaSuccess || (e = cudaMalloc((void**)&E.W2, nm)) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.part, (size_t)E.nchunks * b * b * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.small, (size_t)b * b * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.theta, (size_t)b * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.Yf, (size_t)nb * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&E.Xs, (size_t)nb * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&Yc[0], (size_t)nb * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&Yc[1], (size_t)nb * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&Yc[2], (size_t)nb * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&coef, (size_t)degree * 3 * sizeof(float))) != cudaSuccess) {
+            fail(e, "spmm_eigs_filtered: workspace");
+            break;
+        }
+        // U = orthonormalised start block; SU = S U; Rayleigh-Ritz
+        copy_block_kernel<<<E.grid, kEigThreads, 0, E.s>>>(V0, b, b, n, E.W, b);
+        if (!E.orthonormalize(0, e)) {
+            if (e != cudaSuccess) fail(e, "spmm_eigs_filtered: orthonormalise");
+            else { set_error("spmm_eigs_filtered: the start block is rank-deficient"); rc = SPMM_ERR_ARG; }
+            break;
+        }
+        std::swap(E.V, E.W);                        // V = U (ld b)
+        std::vector<double> T, th, Y, Rn, thk((size_t)b), best_res((size_t)b, 0.0);
+        int it = 0;
+        for (;; ++it) {
+            if ((rc = E.apply_block(E.V, b, E.AV, b)) != SPMM_OK) break;
+            if ((e = E.tn(E.V, b, b, E.AV, b, b, T)) != cudaSuccess) { fail(e, "spmm_eigs_filtered: projection"); break; }
+            for (int i = 0; i < b; ++i)
+                for (int j = i + 1; j < b; ++j) {
+                    const double a = 0.5 * (T[(size_t)i * b + j] + T[(size_t)j * b + i]);
+                    T[(size_t)i * b + j] = a;
+                    T[(size_t)j * b + i] = a;
+                }
+            jacobi_eigh(b, T, th, Y);
+            std::vector<int> order(b);
+            for (int i = 0; i < b; ++i) order[i] = i;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return th[x] > th[y]; });
+            std::vector<double> Yk((size_t)b * b);
+            for (int c = 0; c < b; ++c) {
+                thk[c] = th[order[c]];
+                for (int r = 0; r < b; ++r) Yk[(size_t)r * b + c] = Y[(size_t)r * b + order[c]];
+            }
+            // Ritz vectors and their images; residual norms
+            if ((e = E.nn(E.V, b, b, Yk, b, E.U, b, 1.0, 0.0)) != cudaSuccess ||
+                (e = E.nn(E.AV, b, b, Yk, b, E.AU, b, 1.0, 0.0)) != cudaSuccess) {
+                fail(e, "spmm_eigs_filtered: Ritz vectors");
+                break;
+            }
+            std::swap(E.V, E.U);
+            std::swap(E.AV, E.AU);
+            cudaMemcpyAsync(E.theta, thk.data(), b * sizeof(double), cudaMemcpyHostToDevice, E.s);
+            residual_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.AV, E.V, E.theta, b, n, E.W2);
+            if ((e = E.tn(E.W2, b, b, E.W2, b, b, Rn)) != cudaSuccess) { fail(e, "spmm_eigs_filtered: residuals"); break; }
+            double worst = 0.0;
+            for (int i = 0; i < b; ++i) best_res[i] = std::sqrt(std::max(0.0, Rn[(size_t)i * b + i]));
+            for (int i = 0; i < nev; ++i) worst = std::max(worst, best_res[i]);
+            if (worst <= tol || it >= max_iters) break;
+            // ---- filter the block: coefficients for this interval
+            const double cut = thk[b - 1], top = thk[0];
+            if (!(cut > lower) || !(top > cut)) {
+                set_error("spmm_eigs_filtered: the block's Ritz values do not lie above the lower bound "
+                          "(give a lower bound of the spectrum, or a larger block)");
+                rc = SPMM_ERR_ARG;
+                break;
+            }
+            const double ee = 0.5 * (cut - lower), cc = 0.5 * (cut + lower), s1 = ee / (top - cc);
+            std::vector<float> cf((size_t)degree * 3);
+            double sj = s1;
+            for (int j = 0; j < degree; ++j) {
+                double al, be, ga;
+                if (j == 0) {
+                    al = s1 / ee;
+                    be = -al * cc;
+                    ga = 0.0;
+                } else {
+                    const double sn = 1.0 / (2.0 / s1 - sj);
+                    al = 2.0 * sn / ee;
+                    be = -al * cc;
+                    ga = -sj * sn;
+                    sj = sn;
+                }
+                cf[(size_t)j * 3] = (float)al;
+                cf[(size_t)j * 3 + 1] = (float)be;
+                cf[(size_t)j * 3 + 2] = (float)ga;
+            }
+            if ((e = cudaMemcpyAsync(coef, cf.data(), cf.size() * sizeof(float), cudaMemcpyHostToDevice, E.s)) !=
+                cudaSuccess) {
+                fail(e, "spmm_eigs_filtered: coefficients");
+                break;
+            }
+            // Y0 = U in FP32
+            f64_to_x_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.V, b, b, n, Yc[0], 0);
+            if (!exec) {
+                // steps 1..d on rotating buffers: Y{j} in Yc[j % 3]
+                cudaGraph_t graph = nullptr;
+                if ((e = cudaStreamBeginCapture(E.s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+                    fail(e, "spmm_eigs_filtered: capture");
+                    break;
+                }
+                for (int j = 0; j < degree && rc == SPMM_OK; ++j) {
+                    float* yc = Yc[j % 3];
+                    float* yp = j > 0 ? Yc[(j + 2) % 3] : nullptr;
+                    float* yn = Yc[(j + 1) % 3];
+                    const void* X = yc;
+                    if (xtype == SPMM_BF16) {
+                        f32_to_bf16_kernel<<<E.grid, kEigThreads, 0, E.s>>>(yc, nb, static_cast<__nv_bfloat16*>(E.Xs));
+                        X = E.Xs;
+                    }
+                    rc = apply_dev(S, 0, X, b, b, xtype, E.Yf, b, E.s);
+                    if (rc == SPMM_OK)
+                        cheb_step_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.Yf, yc, yp, yn, nb, coef + (size_t)j * 3);
+                }
+                const cudaError_t ec = cudaStreamEndCapture(E.s, &graph);
+                if (rc == SPMM_OK && ec != cudaSuccess) fail(ec, "spmm_eigs_filtered: end capture");
+                if (rc == SPMM_OK && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) {
+                    exec = nullptr;
+                    fail(e, "spmm_eigs_filtered: instantiate");
+                }
+                if (graph) cudaGraphDestroy(graph);
+                if (rc != SPMM_OK) break;
+            }
+            if ((e = cudaGraphLaunch(exec, E.s)) != cudaSuccess) { fail(e, "spmm_eigs_filtered: filter"); break; }
+            // the filtered block, orthonormalised, is the next U
+            f32_to_f64_kernel<<<E.grid, kEigThreads, 0, E.s>>>(Yc[degree % 3], b, n, E.W, b);
+            if (!E.orthonormalize(0, e)) {
+                if (e != cudaSuccess) fail(e, "spmm_eigs_filtered: orthonormalise");
+                else {
+                    set_error("spmm_eigs_filtered: the filtered block lost rank (lower the degree)");
+                    rc = SPMM_ERR_ARG;
+                }
+                break;
+            }
+            std::swap(E.V, E.W);
+        }
+        if (rc != SPMM_OK) break;
+        for (int i = 0; i < nev; ++i) {
+            evals[i] = thk[i];
+            if (resid) resid[i] = best_res[i];
+        }
+        if (evecs) copy_block_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.V, b, nev, n, evecs, nev);
+        if (iters_out) *iters_out = it;
+        if ((e = cudaStreamSynchronize(E.s)) != cudaSuccess) { fail(e, "spmm_eigs_filtered: run"); break; }
+        int32_t st = 0;
+        if ((e = cudaMemcpy(&st, S->status, sizeof(st), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            fail(e, "spmm_eigs_filtered: status");
+            break;
+        }
+        if (st != 0) {
+            cudaMemset(S->status, 0, sizeof(int32_t));
+            set_error("spmm_eigs_filtered: a device-side staging wait timed out; the result is incomplete");
+            rc = SPMM_ERR_TIMEOUT;
+        }
+    } while (0);
+    if (E.s) {
+        cudaStreamSynchronize(E.s);
+        cudaStreamDestroy(E.s);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaFree(E.V); cudaFree(E.AV); cudaFree(E.U); cudaFree(E.AU); cudaFree(E.W); cudaFree(E.W2);
+    cudaFree(E.part); cudaFree(E.small); cudaFree(E.theta); cudaFree(E.Yf); cudaFree(E.Xs);
+    cudaFree(Yc[0]); cudaFree(Yc[1]); cudaFree(Yc[2]); cudaFree(coef);
+    return rc;
+}
+
+extern "C" int spmm_eigs_filtered(spmm_mat_t S, int32_t nev, int32_t block, int32_t degree, double lower,
+                                  int32_t max_iters, double tol, spmm_dtype xtype, const double* V0, double* evals,
+                                  double* evecs, double* resid, int32_t* iters_out, void* stream) {
+    return eigs_filtered_impl(S, nev, block, degree, lower, max_iters, tol, xtype, V0, evals, evecs, resid, iters_out,
+                              stream);
 }

@@ -88,6 +88,9 @@ _lib.spmm_apply_csr_static.argtypes = [_i64, _i64, _i64, _P, _P, _P, ctypes.c_in
 _lib.spmm_apply_csr_static.restype = ctypes.c_int
 _lib.spmm_apply_batched.argtypes = [_i32, _P, _P, _P, _P, ctypes.c_int, _i32, _P]
 _lib.spmm_apply_batched.restype = ctypes.c_int
+_lib.spmm_eigs_filtered.argtypes = [_P, _i32, _i32, _i32, ctypes.c_double, _i32, ctypes.c_double, ctypes.c_int, _P,
+                                    _P, _P, _P, _P, _P]
+_lib.spmm_eigs_filtered.restype = ctypes.c_int
 _lib.spmm_static_status.argtypes = [_P]
 _lib.spmm_static_status.restype = ctypes.c_int
 _lib.spmm_pagerank.argtypes = [_P, ctypes.c_double, _i32, _P, _P, _P, _P]
@@ -314,6 +317,19 @@ def spmm_eigs(h, nev, V0, block=16, max_basis=64, max_restarts=100, tol=1e-6, xt
     return ev, rs, nr.value
 
 
+def spmm_eigs_filtered(h, nev, V0, degree=20, lower=-1.0, max_iters=100, tol=1e-6, xtype=SPMM_F32, evecs=None,
+                       stream=None):
+    """Top-nev eigenpairs by Chebyshev-filtered subspace iteration; V0 is a
+    float64 CUDA tensor (n x block).  Returns (evals, residuals, iterations)."""
+    ev = np.zeros(nev, dtype=np.float64)
+    rs = np.zeros(nev, dtype=np.float64)
+    ni = ctypes.c_int32(0)
+    _check(_lib.spmm_eigs_filtered(h, int(nev), int(V0.shape[1]), int(degree), float(lower), int(max_iters),
+                                   float(tol), int(xtype), _ptr(V0), _P(ev.ctypes.data), _ptr(evecs),
+                                   _P(rs.ctypes.data), ctypes.byref(ni), _stream_handle(stream)))
+    return ev, rs, ni.value
+
+
 def spmm_replan(h, opts: spmm_opts | None = None, transpose=0, stream=None):
     _check(_lib.spmm_replan(h, ctypes.byref(opts) if opts is not None else None, int(transpose),
                             _stream_handle(stream)))
@@ -521,6 +537,11 @@ class SparseMatrix:
     def eigs(self, nev, V0, **kw):
         """Top-nev eigenpairs of a symmetric matrix: (evals, residuals, restarts)."""
         return spmm_eigs(self.handle, nev, V0, **kw)
+
+    def eigs_filtered(self, nev, V0, **kw):
+        """Top-nev eigenpairs by Chebyshev-filtered subspace iteration:
+        (evals, residuals, iterations)."""
+        return spmm_eigs_filtered(self.handle, nev, V0, **kw)
 
     def nmf(self, k, steps, W, Ht, ftype=SPMM_F32, eps=1e-12, stream=None):
         """NMF in place on W (rows x k) and Ht (cols x k); returns objective."""

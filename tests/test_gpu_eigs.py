@@ -106,3 +106,59 @@ def test_svds_matches_oracle(sp):
         np.testing.assert_allclose(np.linalg.norm(Av, axis=0), sv, rtol=1e-5)
     finally:
         h.close()
+
+
+def test_filtered_cycle_closed_form(sp):
+    n = 200
+    i = np.arange(n)
+    C = graphs.csr_from_edges(n, n, np.r_[i, (i + 1) % n], np.r_[(i + 1) % n, i], np.full(2 * n, 0.5))
+    h = sp.SparseMatrix.from_csr(C)
+    try:
+        ev, res, it = h.eigs_filtered(8, start_block(n, 16), degree=10, lower=-1.0, max_iters=400, tol=1e-6)
+        expect = np.sort(np.cos(2 * np.pi * np.arange(n) / n))[::-1][:8]
+        np.testing.assert_allclose(ev, expect, atol=2e-6)
+        assert np.all(res <= 1e-6), res
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("xdtype,tol,atol", [("f32", 1e-6, 2e-6), ("bf16", 5e-3, 2e-3)])
+def test_filtered_rmat_lcc_matches_oracle(sp, lcc12, xdtype, tol, atol):
+    """Chebyshev-filtered subspace iteration on the normalised R-MAT LCC:
+    eigenvalues against the FP64 oracle's Lanczos, true residuals through the
+    oracle's product, orthonormal vectors."""
+    import torch
+    S = lcc12
+    n = S.n_rows
+    h = sp.SparseMatrix.from_csr(S)
+    try:
+        evecs = torch.zeros((n, 8), dtype=torch.float64, device="cuda")
+        xt = sp.SPMM_F32 if xdtype == "f32" else sp.SPMM_BF16
+        ev, res, it = h.eigs_filtered(8, start_block(n, 16), degree=16, lower=-1.0, max_iters=300, tol=tol,
+                                      xtype=xt, evecs=evecs)
+        Q0 = synth.dense(n, 8, seed=9).astype(np.float64)
+        evr, _, _ = oracle.lanczos(n, S.row_ptr, S.col_idx, S.values, Q0, 8, 400)
+        np.testing.assert_allclose(ev, evr, atol=atol)
+        assert np.all(res <= tol), res
+        U = evecs.cpu().numpy()
+        SU = oracle.spmm(n, n, S.row_ptr, S.col_idx, S.values, U)
+        true_res = np.linalg.norm(SU - U * ev[None, :], axis=0)
+        assert np.all(true_res <= 20 * tol), true_res
+        np.testing.assert_allclose(U.T @ U, np.eye(8), atol=1e-8 if xdtype == "f32" else 1e-6)
+    finally:
+        h.close()
+
+
+def test_filtered_argument_errors(sp):
+    n = 100
+    C = graphs.cycle(n)
+    h = sp.SparseMatrix(n, n, C.row_ptr, C.col_idx, None)
+    try:
+        with pytest.raises(sp.SpmmError):                   # block must exceed nev
+            h.eigs_filtered(8, start_block(n, 8), degree=4)
+        with pytest.raises(sp.SpmmError):                   # degree 0
+            h.eigs_filtered(4, start_block(n, 8), degree=0)
+        with pytest.raises(sp.SpmmError):                   # the lower bound lies above the block's Ritz values
+            h.eigs_filtered(4, start_block(n, 8), degree=4, lower=5.0, tol=1e-12)
+    finally:
+        h.close()

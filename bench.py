@@ -1068,6 +1068,15 @@ def main():
         cpu["single_thread"] = {"value": nz1 * len(ks) / dt1, "unit": UNIT, "cores": 1,
                                 "sample": f"{len(rows1)} seeded rows ({nz1} nonzeros), every k in the sweep, "
                                           f"no PageRank ({dt1:.1f} s)"}
+        # per k, on the one-thread sample: all cores and one thread
+        cpu["per_k"] = {}
+        for k in ks:
+            r = {}
+            for th in (threads, 1):
+                t0 = time.perf_counter()
+                oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xh, rows1, threads=th, k=k)
+                r["all_cores" if th == threads else "one_thread"] = nz1 / (time.perf_counter() - t0)
+            cpu["per_k"][str(k)] = r
 
     # ---- streaming mode on a smaller graph (R-MAT scale 26, avg degree 32,
     # 8.95 GB of CSR in pinned host memory): link GB/s against the measured

@@ -124,6 +124,20 @@ def test_sym_rmat25_lcc_spmm_and_eigensolver(sp):
     np.testing.assert_allclose(rq, ev, atol=1e-5)
     R = torch.linalg.norm(SV - V * torch.from_numpy(ev).cuda(), dim=0).cpu().numpy()
     np.testing.assert_allclose(R, rs, rtol=0.05, atol=1e-5)
+    # the filtered subspace iteration converges here (the restarted Krylov
+    # method does not within its restarts): residuals <= 1e-5 through the
+    # FP32 product, orthonormal vectors, Rayleigh quotients = eigenvalues
+    V.zero_()
+    ev, rs, it = h.eigs_filtered(8, V0, degree=20, lower=-1.0, max_iters=60, tol=1e-5, evecs=V)
+    assert np.all(rs <= 1e-5), rs
+    assert abs(ev[0] - 1.0) < 1e-6 and np.all(np.diff(ev) <= 0)
+    G = (V.T @ V).cpu().numpy()
+    assert np.max(np.abs(G - np.eye(8))) < 1e-8
+    SV = h.apply(V.float()).double()
+    rq = (V * SV).sum(dim=0).cpu().numpy()
+    np.testing.assert_allclose(rq, ev, atol=1e-6)
+    R = torch.linalg.norm(SV - V * torch.from_numpy(ev).cuda(), dim=0).cpu().numpy()
+    assert np.all(R <= 2e-5), R
     h.close()
 
 

@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--record-traffic", default=None, metavar="CSV",
                     help="write the traffic record from an ncu raw CSV export of one rows_kernel launch, then exit")
     ap.add_argument("--pagerank-iters", type=int, default=30)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the eigensolver (scale 18) and 256-graph batch sub-records of the default line")
     ap.add_argument("--eigs-krylov-full", action="store_true",
                     help="eigs workload: also run the Krylov-Schur solver at full size (300 restarts)")
     ap.add_argument("--workload", default="ksweep",
@@ -631,9 +633,10 @@ def workload_file(args):
                       "timing": "wall clock per apply incl. the file reads (median of --steps)"})
 
 
-def workload_nmf_batched(args):
+def workload_nmf_batched(args, nmf_ks=(8, 16, 32)):
     """256 Chung-Lu graphs in one block-diagonal handle: batched SpMM vs one
-    launch per graph, then NMF (k = 8, 16, 32; 50 steps; FP32 and BF16)."""
+    launch per graph, then NMF (k = 8, 16, 32 by default; 50 steps; FP32 and
+    BF16)."""
     import torch
     import oracle
     from paper_1602_02864_gb300 import spmm
@@ -690,7 +693,7 @@ def workload_nmf_batched(args):
         s_.close()
     nmf = {}
     steps = 50
-    for kk in (8, 16, 32):
+    for kk in nmf_ks:
         for ft, name in ((spmm.SPMM_F32, "f32"), (spmm.SPMM_BF16, "bf16")):
             W0 = torch.from_numpy(np.concatenate([synth.dense(g.n_rows, kk, seed=1000 + i, mode="unit") + 0.01
                                                   for i, g in enumerate(graphs)])).cuda()
@@ -732,15 +735,38 @@ def workload_nmf_batched(args):
                       "graphs": n_graphs, "vertices": nv, "nnz": nnz, "nmf_50_steps": nmf})
 
 
-def workload_eigs(args):
+def eigs_reference(S, scale):
+    """The FP64 oracle's top-8 eigenvalues of this scale-18 graph from
+    tests/golden (written by tests/golden/make_eigs_reference.py, which calls
+    only the oracle), if the file describes this very matrix; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "tests", "golden", f"eigs_symrmat_lcc{scale}_top8.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for a in (np.ascontiguousarray(S.row_ptr, dtype=np.int64), np.ascontiguousarray(S.col_idx, dtype=np.int32),
+              np.ascontiguousarray(S.values, dtype=np.float32)):
+        h.update(a.tobytes())
+    if rec["graph"]["csr_sha256"] != h.hexdigest():
+        return None
+    return np.asarray(rec["evals"], dtype=np.float64)
+
+
+def workload_eigs(args, scales=None):
     """Top 8 eigenpairs of the normalised symmetrised R-MAT graph (largest
     component), block 16: FP32 vs BF16 SpMM inputs; errors vs the FP64 oracle
-    at scale 18."""
+    at scale 18 (its stored eigenvalues when they match the graph, else a
+    fresh oracle run)."""
     import torch
     import oracle
     from paper_1602_02864_gb300 import spmm
     out = {}
-    for scale in (18, args.scale if args.scale != 24 else 25):
+    if scales is None:
+        scales = (18, args.scale if args.scale != 24 else 25)
+    for scale in scales:
         t = time.time()
         S = synth.sym_rmat_lcc(scale, seed=0)
         t_gen = time.time() - t
@@ -757,9 +783,12 @@ def workload_eigs(args):
                "bf16_spmm_speedup": ms32 / ms16, "generate_s": round(t_gen, 1)}
         ref = None
         if scale == 18:
-            Q0 = synth.dense(n, 8, seed=9).astype(np.float64)
-            # a plain Lanczos needs a large basis on this clustered spectrum (240 was not enough)
-            ref, _, _ = oracle.lanczos(n, S.row_ptr, S.col_idx, S.values, Q0, 8, 520)
+            ref = eigs_reference(S, scale)
+            res["oracle_reference"] = "tests/golden (stored oracle run)" if ref is not None else "oracle run"
+            if ref is None:
+                Q0 = synth.dense(n, 8, seed=9).astype(np.float64)
+                # a plain Lanczos needs a large basis on this clustered spectrum (240 was not enough)
+                ref, _, _ = oracle.lanczos(n, S.row_ptr, S.col_idx, S.values, Q0, 8, 1000)
         for xt, name, tol in ((spmm.SPMM_F32, "f32", 1e-6 if scale <= 20 else 1e-5), (spmm.SPMM_BF16, "bf16", 5e-3)):
             # block Krylov-Schur (Section 4.2's method); at scale 25 only with
             # --eigs-krylov-full (it does not converge within 300 restarts there)
@@ -1092,6 +1121,31 @@ def main():
                      "link": sl["link"], "bit_identical_to_resident": sl["bit_identical_to_resident"],
                      "sampled_rows_max_err_over_absprod": sl["sampled_rows_max_err_over_absprod"]}
 
+    # ---- the other configurations, compact: the eigensolver's errors against
+    # the FP64 oracle at scale 18 and the 256-graph batch (one launch, the
+    # batched call over separate handles, NMF k = 16)
+    configs = None
+    if rank == 0 and not args.no_configs:
+        if h.handle is not None:
+            h.close()
+        torch.cuda.empty_cache()
+        cargs = argparse.Namespace(**vars(args))
+        cargs.steps, cargs.warmup = 5, 2
+        t0 = time.time()
+        eg = workload_eigs(cargs, scales=(18,))["results"]["scale18"]
+        t_eigs = time.time() - t0
+        t0 = time.time()
+        nb = workload_nmf_batched(cargs, nmf_ks=(16,))
+        t_nmf = time.time() - t0
+        configs = {
+            "eigs_symrmat_lcc18": dict(eg, wall_s=round(t_eigs, 1)),
+            "chunglu256_batched": {"nnz_per_s": nb["value"], "ms_per_call": nb["ms_per_step"],
+                                   "wall_s": round(t_nmf, 1),
+                                   **{key: nb[key] for key in ("per_graph_launches_ms", "batched_speedup",
+                                                               "bit_identical", "spmm_apply_batched", "graphs",
+                                                               "vertices", "nnz", "nmf_50_steps")}},
+        }
+
     if rank == 0:
         line = {
             "metric": metric_name(args), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1117,6 +1171,7 @@ def main():
                                        "nnz/s over that"},
             "e2e": e2e,
             "streaming": streaming,
+            "configs": configs,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "gpu_launches": (launches_per_apply * len(ks) + launches_per_pr_iter * args.pagerank_iters

@@ -162,3 +162,25 @@ def test_filtered_argument_errors(sp):
             h.eigs_filtered(4, start_block(n, 8), degree=4, lower=5.0, tol=1e-12)
     finally:
         h.close()
+
+
+def test_filtered_scale18_vs_stored_oracle(sp):
+    """Section 4.2's eigenproblem at the size the precision configuration
+    reports its errors on (normalised symmetrised R-MAT LCC, scale 18): the
+    FP32 filtered solve against the FP64 oracle's stored eigenvalues."""
+    import json
+    import os
+    import torch
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "eigs_symrmat_lcc18_top8.json")) as f:
+        rec = json.load(f)
+    S = synth.sym_rmat_lcc(18, seed=0)
+    assert (S.n_rows, S.nnz) == (rec["graph"]["n"], rec["graph"]["nnz"])
+    h = sp.SparseMatrix.from_csr(S)
+    try:
+        ev, res, it = h.eigs_filtered(8, start_block(S.n_rows, 16, seed=1), degree=20, lower=-1.0, max_iters=300,
+                                      tol=1e-6)
+        assert np.all(res <= 1e-6), res
+        np.testing.assert_allclose(ev, rec["evals"], rtol=0, atol=2e-7)
+    finally:
+        h.close()

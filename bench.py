@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--record-traffic", default=None, metavar="CSV",
                     help="write the traffic record from an ncu raw CSV export of one rows_kernel launch, then exit")
     ap.add_argument("--pagerank-iters", type=int, default=30)
+    ap.add_argument("--no-relabel", action="store_true",
+                    help="skip the sub-record of the same sweep on a handle made with SPMM_RELABEL")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the eigensolver (scale 18) and 256-graph batch sub-records of the default line")
     ap.add_argument("--eigs-krylov-full", action="store_true",
@@ -1079,6 +1081,48 @@ def main():
                "results_match_device": bool(ok)}
         del Xp, Yp
 
+    # ---- the same sweep and PageRank on a handle made with SPMM_RELABEL
+    # (vertices by decreasing degree): the products with the vectors kept in
+    # the handle's order (spmm_apply_relabelled), PageRank through its public
+    # call (ranks in and out of the input order once per call), and the first
+    # k's result brought back to the input order against this run's Y
+    relabelled = None
+    if rank == 0 and not args.no_relabel:
+        t0 = time.time()
+        hr = spmm.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, transpose=args.pagerank_iters > 0,
+                               relabel=True)
+        torch.cuda.synchronize()
+        t_rl = time.time() - t0
+        per = {}
+        for k in ks:
+            Xr = hr.to_handle_order(X[k])
+            Yr = torch.empty((N, k), dtype=torch.float32, device=dev)
+            ms = event_ms(lambda: hr.apply_relabelled(Xr, Y=Yr), args.steps, flush)
+            B = alg_bytes(nnz, N, N, k, 4)
+            d = (hr.to_input_order(Yr) - Y[k]).abs().max().item() / max(Y[k].abs().max().item(), 1e-30)
+            per[str(k)] = {"ms": round(ms, 4), "speedup_vs_input_order": breakdown[str(k)]["ms"] / ms,
+                           "nnz_per_s": nnz / (ms / 1e3), "roofline_frac": B / (ms / 1e3) / 1e9 / peak_gbs,
+                           "max_diff_vs_input_order_result": d}
+            del Xr, Yr
+        pr_rl = None
+        if args.pagerank_iters:
+            xrl = torch.empty(N, dtype=torch.float32, device=dev)
+            hr.pagerank(0.85, args.pagerank_iters, x=xrl)
+            ms = event_ms(lambda: hr.pagerank(0.85, args.pagerank_iters, x=xrl), args.steps)
+            pr_rl = {"ms": round(ms, 3), "speedup_vs_input_order": pagerank["ms"] / ms,
+                     "max_rel_diff_vs_input_order_ranks":
+                         float(((xrl - xpr).abs() / xpr.abs().clamp_min(1e-30)).max().item())}
+            del xrl
+        rl_ms = sum(v["ms"] for v in per.values()) + (pr_rl["ms"] if pr_rl else 0.0)
+        relabelled = {"order": "vertices by decreasing row + column entry count (SPMM_RELABEL)",
+                      "create_s": round(t_rl, 2), "per_k": per, "pagerank": pr_rl,
+                      "step_ms": round(rl_ms, 3),
+                      "nnz_per_s_step": nnz * (len(ks) + args.pagerank_iters) / (rl_ms / 1e3),
+                      "note": "products with X and Y kept in the handle's vertex order; not the headline, "
+                              "which multiplies in the input order"}
+        hr.close()
+        torch.cuda.empty_cache()
+
     # ---- CPU baseline: the oracle on a bounded row sample, all host cores
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -1172,6 +1216,7 @@ def main():
                                        "nnz/s over that"},
             "e2e": e2e,
             "streaming": streaming,
+            "relabelled": relabelled,
             "configs": configs,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),

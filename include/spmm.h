@@ -57,6 +57,7 @@ typedef enum {
 #define SPMM_HOST_STREAMING 0x2u   /* keep A in host memory and stream it per call (A X only) */
 #define SPMM_REORDER 0x4u          /* relabel columns by decreasing degree (see spmm_create_csr) */
 #define SPMM_FILE_DIRECT 0x8u      /* spmm_create_file: read with O_DIRECT (bypass the page cache) */
+#define SPMM_RELABEL 0x10u         /* renumber the vertices of a square matrix by decreasing degree */
 
 /* Tuning knobs of the warp-task plan (the GPU form of the paper's tile-row
  * batches, Section 3.4); a NULL pointer or a zero field selects the default.
@@ -133,7 +134,7 @@ typedef struct {
     int32_t value_dtype;         /* spmm_dtype of the stored values, -1 = pattern   */
     int32_t has_transpose;
     int32_t n_graphs;            /* graphs in a batched handle (1 otherwise)        */
-    int32_t reserved;
+    int32_t relabelled;          /* 1: made with SPMM_RELABEL                       */
     /* Row-walk efficiency of the forward plan's short-row runs for 2, 4, 8
      * and 16 lane groups per warp (X rows on 16, 8, 4 and 2 lanes): group g
      * takes rows g, g+G, ... of a run, one round is one row per group and
@@ -161,13 +162,16 @@ typedef struct {
  *   col_idx    nnz int32, 0 <= col < n_cols (any order within a row)
  *   values     nnz values of type vtype, or NULL for a pattern matrix (all 1)
  *   vtype      SPMM_F32, SPMM_BF16 or SPMM_F16 (ignored when values is NULL)
- *   flags      SPMM_WANT_TRANSPOSE, SPMM_HOST_STREAMING, SPMM_REORDER (or'd), or 0
+ *   flags      SPMM_WANT_TRANSPOSE, SPMM_HOST_STREAMING, SPMM_REORDER, SPMM_RELABEL
+ *              (or'd), or 0
  *   opts       tuning knobs or NULL
  *   stream     stream for the copies; the call returns after they finish
  * Errors: SPMM_ERR_ARG (null/shape), SPMM_ERR_FORMAT (row_ptr not monotone,
  * wrong row_ptr[0] or row_ptr[n_rows], column out of range), SPMM_ERR_OOM,
- * SPMM_ERR_UNSUPPORTED (streaming with SPMM_WANT_TRANSPOSE or SPMM_REORDER),
- * SPMM_ERR_CUDA.  The input arrays are copied; the caller keeps ownership.
+ * SPMM_ERR_UNSUPPORTED (streaming with SPMM_WANT_TRANSPOSE, SPMM_REORDER or
+ * SPMM_RELABEL), SPMM_ERR_CUDA; SPMM_ERR_ARG also for SPMM_RELABEL with a
+ * non-square matrix or with SPMM_REORDER.  The input arrays are copied; the
+ * caller keeps ownership.
  *
  * SPMM_REORDER (Section 5.1: the vertex order decides how well gathered rows
  * stay in cache): each orientation's columns are relabelled by decreasing
@@ -181,6 +185,23 @@ typedef struct {
  * a contiguous (ldx = k), 16-byte-aligned array -- the layout of the
  * relabelled copy.  A strided or misaligned X can give another summation
  * order (the kernel's vector width follows X's alignment).
+ *
+ * SPMM_RELABEL (Section 5.1 again, for square matrices): the handle stores
+ * B = P A P^T, where P renumbers the vertices by decreasing total degree
+ * (stored entries in the vertex's row plus those in its column; ties keep the
+ * vertex order, spmm_relabel_order), and each row of B keeps its entries in
+ * increasing new column order.  The most-gathered rows of X then share L2
+ * lines and each warp task gathers from a narrower band of X (R-MAT scale 24:
+ * 8-25% faster from k = 2 on, with the vectors in the new order).  Vectors in
+ * the new order ("the handle's order") go to spmm_apply_relabelled at no
+ * extra cost; spmm_apply keeps the input order by gathering X's rows into the
+ * handle's order and Y's rows back (two buffers the handle keeps and grows,
+ * n * k elements each).  spmm_pagerank, spmm_eigs, spmm_eigs_filtered,
+ * spmm_svds and spmm_nmf take and return vectors in the input order and run
+ * in the handle's order in between.  The new summation order within a row
+ * gives other float32 roundings than a handle without the flag.  Not with
+ * spmm_create_batched, spmm_apply_batched or the host-buffer calls
+ * (spmm_apply_host, spmm_apply_host_parts: SPMM_ERR_UNSUPPORTED).
  *
  * Streaming mode (SPMM_HOST_STREAMING; Section 3.1 keeps the sparse matrix
  * outside memory and streams it while the dense matrices stay resident, and
@@ -264,8 +285,9 @@ int spmm_create_batched(spmm_mat_t* out, int32_t n_graphs, const int64_t* n_rows
  *          k columns of each row are written
  * Accumulation is float32 in a fixed order: repeated calls give bit-identical
  * results.  Asynchronous on `stream`; allocates nothing, except that a handle
- * made with SPMM_REORDER grows its relabelled-X buffer the first time a
- * larger n * k is used (which waits for the device), and a handle made by
+ * made with SPMM_REORDER grows its relabelled-X buffer (SPMM_RELABEL: its X
+ * and Y buffers) the first time a larger n * k is used (which waits for the
+ * device), and a handle made by
  * spmm_create_file blocks the calling thread until every block of the matrix
  * has been read from its file.
  * Errors: SPMM_ERR_ARG (null, k out of range, ld < k, dtype, transpose without
@@ -275,6 +297,50 @@ int spmm_create_batched(spmm_mat_t* out, int32_t n_graphs, const int64_t* n_rows
  */
 int spmm_apply(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype xtype, void* Y,
                int64_t ldy, spmm_dtype ytype, int32_t transpose, void* stream);
+
+/*
+ * spmm_apply_relabelled -- spmm_apply with X and Y in the handle's vertex
+ * order (SPMM_RELABEL): Y' = B X' with B = P A P^T, X' = P X, Y' = P Y, so a
+ * computation that keeps its vectors in that order (convert them once with
+ * spmm_relabel_rows) pays nothing for the relabelling.  Arguments, errors and
+ * asynchrony as spmm_apply; allocates nothing.  On a handle made without
+ * SPMM_RELABEL it is spmm_apply.
+ */
+int spmm_apply_relabelled(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype xtype, void* Y,
+                          int64_t ldy, spmm_dtype ytype, int32_t transpose, void* stream);
+
+/*
+ * spmm_relabel_rows -- convert the n x k rows of a dense matrix between the
+ * input vertex order and the handle's order (n = the handle's rows; square
+ * handles only):
+ *   to_handle_order != 0:  dst[v'] = src[old_of_new[v']]   (input -> handle)
+ *   to_handle_order == 0:  dst[v]  = src[new_of_old[v]]    (handle -> input)
+ * src, dst  device, row-major, leading dimensions ld_src, ld_dst >= k, element
+ *           type dtype (F32, BF16, F16 or F64); they must not overlap
+ * Without SPMM_RELABEL it copies.  Asynchronous on `stream`; allocates
+ * nothing.  Errors: SPMM_ERR_ARG (NULL, non-square handle, k < 1, ld < k,
+ * dtype, src == dst), SPMM_ERR_CUDA.
+ */
+int spmm_relabel_rows(spmm_mat_t A, const void* src, int64_t ld_src, int32_t k, spmm_dtype dtype, void* dst,
+                      int64_t ld_dst, int32_t to_handle_order, void* stream);
+
+/*
+ * spmm_get_relabel -- the handle's vertex order: old_of_new[v'] (host int32,
+ * n entries) is the input vertex that is vertex v' of the handle; the
+ * identity without SPMM_RELABEL.  Synchronous.  Errors: SPMM_ERR_ARG (NULL),
+ * SPMM_ERR_CUDA.
+ */
+int spmm_get_relabel(spmm_mat_t A, int32_t* old_of_new);
+
+/*
+ * spmm_relabel_order -- host-only: the order SPMM_RELABEL gives an n x n CSR
+ * matrix.  Vertex v has degree (row_ptr[v+1] - row_ptr[v]) + (entries with
+ * column v); old_of_new lists the vertices by decreasing degree, equal degrees
+ * in increasing vertex order.  No GPU is used.  Errors: SPMM_ERR_ARG (n out of
+ * range, NULL), SPMM_ERR_FORMAT (row_ptr[0] != 0, decreasing row_ptr, column
+ * out of range), SPMM_ERR_OOM.
+ */
+int spmm_relabel_order(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int32_t* old_of_new);
 
 /*
  * spmm_apply_batched -- Y_i = A_i X_i (or A_i^T X_i) for n handles, each with

@@ -282,16 +282,25 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
         return SPMM_ERR_ARG;
     }
     if (!row_ptr || (nnz > 0 && !col_idx)) { set_error(w + ": row_ptr/col_idx is NULL"); return SPMM_ERR_ARG; }
-    if (flags & ~(SPMM_WANT_TRANSPOSE | SPMM_HOST_STREAMING | SPMM_REORDER)) {
+    if (flags & ~(SPMM_WANT_TRANSPOSE | SPMM_HOST_STREAMING | SPMM_REORDER | SPMM_RELABEL)) {
         set_error(w + ": unknown flag bits");
         return SPMM_ERR_ARG;
     }
-    if ((flags & SPMM_HOST_STREAMING) && (flags & (SPMM_WANT_TRANSPOSE | SPMM_REORDER))) {
+    if ((flags & SPMM_HOST_STREAMING) && (flags & (SPMM_WANT_TRANSPOSE | SPMM_REORDER | SPMM_RELABEL))) {
         set_error(w + ": the streaming mode computes A X only, without relabelling "
-                      "(no SPMM_WANT_TRANSPOSE or SPMM_REORDER)");
+                      "(no SPMM_WANT_TRANSPOSE, SPMM_REORDER or SPMM_RELABEL)");
         return SPMM_ERR_UNSUPPORTED;
     }
     const bool reorder = (flags & SPMM_REORDER) != 0;
+    const bool relabel = (flags & SPMM_RELABEL) != 0;
+    if (relabel && reorder) {
+        set_error(w + ": SPMM_RELABEL and SPMM_REORDER exclude each other");
+        return SPMM_ERR_ARG;
+    }
+    if (relabel && n_rows != n_cols) {
+        set_error(w + ": SPMM_RELABEL renumbers the vertices of a square matrix");
+        return SPMM_ERR_ARG;
+    }
     size_t vsize = 0;
     if (values) {
         if (vtype != SPMM_F32 && vtype != SPMM_BF16 && vtype != SPMM_F16) {
@@ -336,6 +345,27 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
     double a2 = 0.0;
     for (int c = 0; c < kChunks; ++c) a2 += a2c[c];
     const Params prm = resolve_params(opts);
+    // SPMM_RELABEL: from here on the matrix is B = P A P^T
+    std::vector<int32_t> rl_old_of_new, rl_new_of_old, rl_ci;
+    std::vector<int64_t> rl_rp;
+    std::vector<char> rl_val;
+    if (relabel) {
+        int rrc = SPMM_OK;
+        try {
+            relabel_order(n_rows, row_ptr, col_idx, rl_old_of_new);
+            rrc = relabel_csr(n_rows, row_ptr, col_idx, values, vsize, rl_old_of_new, rl_new_of_old, rl_rp, rl_ci,
+                              rl_val);
+        } catch (const std::bad_alloc&) {
+            rrc = SPMM_ERR_OOM;
+        }
+        if (rrc != SPMM_OK) {
+            set_error(w + ": out of host memory for the relabelled matrix");
+            return rrc;
+        }
+        row_ptr = rl_rp.data();
+        col_idx = rl_ci.data();
+        if (values) values = rl_val.data();
+    }
 
     spmm_mat* A = new (std::nothrow) spmm_mat();
     if (!A) { set_error(w + ": out of host memory"); return SPMM_ERR_OOM; }
@@ -400,9 +430,27 @@ static int create_impl(spmm_mat** out, int64_t n_rows, int64_t n_cols, int64_t n
             A->has_tr = (rc == SPMM_OK);
         }
     }
+    if (rc == SPMM_OK && relabel) {
+        const size_t pb = (size_t)n_rows * sizeof(int32_t);
+        cudaError_t e = cudaMalloc((void**)&A->rl_old_of_new, pb);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&A->rl_new_of_old, pb);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(A->rl_old_of_new, rl_old_of_new.data(), pb, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(A->rl_new_of_old, rl_new_of_old.data(), pb, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, (w + ": vertex order").c_str());
+        } else {
+            A->relabel = true;
+            A->device_bytes += 2 * (int64_t)pb;
+        }
+    }
     if (rc != SPMM_OK) {
         free_dev(A->fwd);
         free_dev(A->tr);
+        cudaFree(A->rl_old_of_new);
+        cudaFree(A->rl_new_of_old);
         cudaFree(A->status);
         delete A;
         return rc;
@@ -506,6 +554,11 @@ extern "C" int spmm_create_batched(spmm_mat_t* out, int32_t n_graphs, const int6
     if (!out || n_graphs < 1 || !n_rows || !n_cols || !row_ptrs || !col_idxs) {
         set_error("spmm_create_batched: NULL argument or n_graphs < 1");
         return SPMM_ERR_ARG;
+    }
+    if (flags & SPMM_RELABEL) {
+        set_error("spmm_create_batched: SPMM_RELABEL is for single square matrices (relabel each graph's "
+                  "vertices before batching)");
+        return SPMM_ERR_UNSUPPORTED;
     }
     const size_t vsize = values ? dtype_size(vtype) : 0;
     std::vector<int64_t> roff((size_t)n_graphs + 1, 0), coff((size_t)n_graphs + 1, 0);
@@ -728,6 +781,27 @@ extern "C" int spmm_apply(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, s
     const DevCSR& d = transpose ? A->tr : A->fwd;
     if (d.n_rows == 0) return SPMM_OK;
     if (!X || !Y) { set_error("spmm_apply: X or Y is NULL"); return SPMM_ERR_ARG; }
+    if (A->relabel) return apply_relabel_io(A, transpose, X, ldx, k, (int32_t)xtype, (float*)Y, ldy, (cudaStream_t)stream);
+    return apply_dev(A, transpose, X, ldx, k, (int32_t)xtype, (float*)Y, ldy, (cudaStream_t)stream);
+}
+
+extern "C" int spmm_apply_relabelled(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype xtype, void* Y,
+                                     int64_t ldy, spmm_dtype ytype, int32_t transpose, void* stream) {
+    if (!A) { set_error("spmm_apply_relabelled: A is NULL"); return SPMM_ERR_ARG; }
+    if (!A->relabel) return spmm_apply(A, X, ldx, k, xtype, Y, ldy, ytype, transpose, stream);
+    if (k < 1 || k > kMaxK) { set_error("spmm_apply_relabelled: k must be in 1..64"); return SPMM_ERR_ARG; }
+    if (ldx < k || ldy < k) { set_error("spmm_apply_relabelled: ldx and ldy must be >= k"); return SPMM_ERR_ARG; }
+    if (ytype != SPMM_F32) { set_error("spmm_apply_relabelled: Y must be F32"); return SPMM_ERR_ARG; }
+    if (xtype != SPMM_F32 && xtype != SPMM_BF16 && xtype != SPMM_F16) {
+        set_error("spmm_apply_relabelled: X must be F32, BF16 or F16");
+        return SPMM_ERR_ARG;
+    }
+    if (transpose && !A->has_tr) {
+        set_error("spmm_apply_relabelled: transpose needs SPMM_WANT_TRANSPOSE at create");
+        return SPMM_ERR_ARG;
+    }
+    if (A->fwd.n_rows == 0) return SPMM_OK;
+    if (!X || !Y) { set_error("spmm_apply_relabelled: X or Y is NULL"); return SPMM_ERR_ARG; }
     return apply_dev(A, transpose, X, ldx, k, (int32_t)xtype, (float*)Y, ldy, (cudaStream_t)stream);
 }
 
@@ -749,6 +823,7 @@ extern "C" int spmm_get_info(spmm_mat_t A, spmm_info* info) {
     info->value_dtype = A->vtype;
     info->has_transpose = A->has_tr ? 1 : 0;
     info->n_graphs = (int32_t)(A->row_off.size() - 1);
+    info->relabelled = A->relabel ? 1 : 0;
     info->n_hot = A->fwd.n_hot;
     info->n_hot_t = A->has_tr ? A->tr.n_hot : 0;
     for (int i = 0; i < 4; ++i) {
@@ -765,6 +840,9 @@ extern "C" int spmm_destroy(spmm_mat_t A) {
     hostio_release(A);
     pagerank_release(A);
     cudaFree(A->xperm);
+    cudaFree(A->yperm);
+    cudaFree(A->rl_old_of_new);
+    cudaFree(A->rl_new_of_old);
     free_dev(A->fwd);
     free_dev(A->tr);
     cudaFree(A->status);

@@ -58,6 +58,10 @@ extern "C" int spmm_apply_batched(int32_t n, const spmm_mat_t* A, const void* co
         if (!M) { set_error(who + ": handle is NULL"); return SPMM_ERR_ARG; }
         if (k[i] < 1 || k[i] > kMaxK) { set_error(who + ": k must be in 1..64"); return SPMM_ERR_ARG; }
         if (M->streaming) { set_error(who + ": streaming handles are not batched"); return SPMM_ERR_UNSUPPORTED; }
+        if (M->relabel) {
+            set_error(who + ": handles with SPMM_RELABEL are not batched");
+            return SPMM_ERR_UNSUPPORTED;
+        }
         if (transpose && !M->has_tr) { set_error(who + ": transpose needs SPMM_WANT_TRANSPOSE"); return SPMM_ERR_ARG; }
         const DevCSR& d = transpose ? M->tr : M->fwd;
         if (d.perm) { set_error(who + ": handles with SPMM_REORDER are not batched"); return SPMM_ERR_UNSUPPORTED; }

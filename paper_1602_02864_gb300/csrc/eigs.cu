@@ -434,18 +434,49 @@ static int eigs_impl(spmm_mat_t S, int op, int32_t nev, int32_t block, int32_t m
     return rc;
 }
 
+// SPMM_RELABEL: the start block (n x block) goes into the handle's vertex
+// order and the vectors (n x nvec) come back, once per call; run(V0, vecs)
+// solves with the pointers it is given.  Other handles call run directly.
+template <class F>
+static int in_handle_order(spmm_mat_t A, int32_t block, const double* V0, int32_t nvec, double* vecs, void* stream,
+                           const char* who, F run) {
+    if (!A || !A->relabel || !V0 || block < 1 || block > 64 || nvec < 1 || nvec > 64) return run(V0, vecs);
+    const int64_t n = A->fwd.n_rows;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *v0r = nullptr, *vr = nullptr;
+    cudaError_t e = cudaMalloc((void**)&v0r, (size_t)n * block * sizeof(double));
+    if (e == cudaSuccess && vecs) e = cudaMalloc((void**)&vr, (size_t)n * nvec * sizeof(double));
+    if (e == cudaSuccess) e = relabel_rows_dev(A, V0, block, block, 8, v0r, block, true, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int rc = e == cudaSuccess ? run(v0r, vr) : cuda_fail(e, who);
+    if (rc == SPMM_OK && vecs) {
+        e = relabel_rows_dev(A, vr, nvec, nvec, 8, vecs, nvec, false, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, who);
+    }
+    cudaFree(v0r);
+    cudaFree(vr);
+    return rc;
+}
+
 extern "C" int spmm_eigs(spmm_mat_t S, int32_t nev, int32_t block, int32_t max_basis, int32_t max_restarts,
                          double tol, spmm_dtype xtype, const double* V0, double* evals, double* evecs,
                          double* resid, int32_t* restarts_out, void* stream) {
-    return eigs_impl(S, 0, nev, block, max_basis, max_restarts, tol, xtype, V0, evals, evecs, resid, restarts_out,
-                     stream);
+    return in_handle_order(S, block, V0, nev, evecs, stream, "spmm_eigs: vectors and the handle's order",
+                           [&](const double* v0, double* vec) {
+                               return eigs_impl(S, 0, nev, block, max_basis, max_restarts, tol, xtype, v0, evals,
+                                                vec, resid, restarts_out, stream);
+                           });
 }
 
 extern "C" int spmm_svds(spmm_mat_t A, int32_t nsv, int32_t block, int32_t max_basis, int32_t max_restarts,
                          double tol, spmm_dtype xtype, const double* V0, double* svals, double* right_vecs,
                          double* resid, int32_t* restarts_out, void* stream) {
-    const int rc = eigs_impl(A, 1, nsv, block, max_basis, max_restarts, tol, xtype, V0, svals, right_vecs, resid,
-                             restarts_out, stream);
+    const int rc = in_handle_order(A, block, V0, nsv, right_vecs, stream, "spmm_svds: vectors and the handle's order",
+                                   [&](const double* v0, double* vec) {
+                                       return eigs_impl(A, 1, nsv, block, max_basis, max_restarts, tol, xtype, v0,
+                                                        svals, vec, resid, restarts_out, stream);
+                                   });
     if (rc == SPMM_OK)
         for (int i = 0; i < nsv; ++i) svals[i] = std::sqrt(std::max(0.0, svals[i]));
     return rc;
@@ -677,6 +708,9 @@ static int eigs_filtered_impl(spmm_mat_t S, int32_t nev, int32_t block, int32_t 
 extern "C" int spmm_eigs_filtered(spmm_mat_t S, int32_t nev, int32_t block, int32_t degree, double lower,
                                   int32_t max_iters, double tol, spmm_dtype xtype, const double* V0, double* evals,
                                   double* evecs, double* resid, int32_t* iters_out, void* stream) {
-    return eigs_filtered_impl(S, nev, block, degree, lower, max_iters, tol, xtype, V0, evals, evecs, resid, iters_out,
-                              stream);
+    return in_handle_order(S, block, V0, nev, evecs, stream, "spmm_eigs_filtered: vectors and the handle's order",
+                           [&](const double* v0, double* vec) {
+                               return eigs_filtered_impl(S, nev, block, degree, lower, max_iters, tol, xtype, v0,
+                                                         evals, vec, resid, iters_out, stream);
+                           });
 }

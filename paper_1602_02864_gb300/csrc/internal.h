@@ -155,6 +155,8 @@ struct PrCache {
     float* x = nullptr;
     double damping = -1.0;
     int32_t iters = -1;
+    // SPMM_RELABEL: the ranks and the start vector in the handle's order
+    float *xr = nullptr, *x0r = nullptr;
 };
 void pagerank_release(spmm_mat* A);
 // drop the captured PageRank graph (the plan or a buffer it uses changed)
@@ -185,8 +187,15 @@ struct spmm_mat {
     bool streaming = false;
     spmm::Streamer st;
     spmm::HostIO hio;
-    void* xperm = nullptr;      // SPMM_REORDER: X with its rows in relabelled order (grow-only)
+    void* xperm = nullptr;      // SPMM_REORDER / SPMM_RELABEL: X with its rows in relabelled order (grow-only)
     size_t xperm_bytes = 0;
+    // SPMM_RELABEL: the vertex order (device) and the result of spmm_apply
+    // before its rows go back to the input order (grow-only)
+    bool relabel = false;
+    int32_t* rl_old_of_new = nullptr;
+    int32_t* rl_new_of_old = nullptr;
+    void* yperm = nullptr;
+    size_t yperm_bytes = 0;
     spmm::PrCache pr;           // spmm_pagerank's workspace and graph (after its first call)
 };
 
@@ -212,6 +221,25 @@ void relabel_by_degree(int64_t n_cols, const int32_t* col_idx, int64_t nnz, std:
 int reorder_reserve(spmm_mat* A, int64_t n_in, int32_t k, int32_t xtype, cudaStream_t s);
 int reorder_x(spmm_mat* A, const DevCSR& d, const void* X, int64_t ldx, int32_t k, int32_t xtype, cudaStream_t s,
               const void** Xp);
+
+// relabel.cu: the vertices of an n x n CSR by decreasing total degree
+// (entries in the row plus entries in the column; ties in vertex order)
+void relabel_order(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, std::vector<int32_t>& old_of_new);
+// B = P A P^T on the host (each row's entries in increasing new column order)
+int relabel_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const void* values, size_t vsize,
+                const std::vector<int32_t>& old_of_new, std::vector<int32_t>& new_of_old, std::vector<int64_t>& rp,
+                std::vector<int32_t>& ci, std::vector<char>& val);
+// dst row r = src row idx[r] (idx == nullptr: row r); k elements of es bytes
+cudaError_t gather_rows(const void* src, int64_t ld_src, const int32_t* idx, int64_t n, int32_t k, int es, void* dst,
+                        int64_t ld_dst, cudaStream_t s);
+// n x k rows between the input order and the handle's order (identity
+// without SPMM_RELABEL)
+cudaError_t relabel_rows_dev(const spmm_mat* A, const void* src, int64_t ld_src, int32_t k, int es, void* dst,
+                             int64_t ld_dst, bool to_handle_order, cudaStream_t s);
+// spmm_apply on an SPMM_RELABEL handle: X's rows into the handle's order, the
+// product, Y's rows back
+int apply_relabel_io(spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
+                     int64_t ldy, cudaStream_t s);
 
 // hot.cu: rank the columns by stored entries (counts, or counted from
 // col_idx when counts is null), keep the max_hot most-referenced ones that

@@ -172,8 +172,8 @@ static void make_chunks(const std::vector<int64_t>& off, std::vector<int4>& chun
 
 using namespace spmm;
 
-extern "C" int spmm_nmf(spmm_mat_t A, int32_t k, int32_t steps, float* W, float* Ht, spmm_dtype ftype, double eps,
-                        double* objective, void* stream) {
+static int nmf_impl(spmm_mat_t A, int32_t k, int32_t steps, float* W, float* Ht, spmm_dtype ftype, double eps,
+                    double* objective, void* stream) {
     if (!A || !W || !Ht) { set_error("spmm_nmf: NULL argument"); return SPMM_ERR_ARG; }
     NvtxRange range("spmm_nmf");
     if (k < 1 || k > kMaxK || steps < 0 || !(eps >= 0.0)) {
@@ -312,5 +312,32 @@ extern "C" int spmm_nmf(spmm_mat_t A, int32_t k, int32_t steps, float* W, float*
     if (s) cudaStreamDestroy(s);
     cudaFree(dchW); cudaFree(dchH); cudaFree(dgW); cudaFree(dgH); cudaFree(part); cudaFree(GW); cudaFree(GH);
     cudaFree(cross); cudaFree(da2); cudaFree(dobj); cudaFree(AtW); cudaFree(AH); cudaFree(fb);
+    return rc;
+}
+
+// SPMM_RELABEL: W and Ht (n x k each) go into the handle's vertex order and
+// come back once per call; the steps run in between.
+extern "C" int spmm_nmf(spmm_mat_t A, int32_t k, int32_t steps, float* W, float* Ht, spmm_dtype ftype, double eps,
+                        double* objective, void* stream) {
+    if (!A || !A->relabel || !W || !Ht || k < 1 || k > kMaxK)
+        return nmf_impl(A, k, steps, W, Ht, ftype, eps, objective, stream);
+    const int64_t n = A->fwd.n_rows;
+    cudaStream_t s = (cudaStream_t)stream;
+    float *wr = nullptr, *hr = nullptr;
+    cudaError_t e = cudaMalloc((void**)&wr, (size_t)n * k * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&hr, (size_t)n * k * sizeof(float));
+    if (e == cudaSuccess) e = relabel_rows_dev(A, W, k, k, 4, wr, k, true, s);
+    if (e == cudaSuccess) e = relabel_rows_dev(A, Ht, k, k, 4, hr, k, true, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int rc = e == cudaSuccess ? nmf_impl(A, k, steps, wr, hr, ftype, eps, objective, stream)
+                              : cuda_fail(e, "spmm_nmf: factors into the handle's order");
+    if (rc == SPMM_OK) {
+        e = relabel_rows_dev(A, wr, k, k, 4, W, k, false, s);
+        if (e == cudaSuccess) e = relabel_rows_dev(A, hr, k, k, 4, Ht, k, false, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "spmm_nmf: factors into the input order");
+    }
+    cudaFree(wr);
+    cudaFree(hr);
     return rc;
 }

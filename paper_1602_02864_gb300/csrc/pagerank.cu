@@ -155,6 +155,8 @@ void pagerank_release(spmm_mat* A) {
     cudaFree(c.part);
     cudaFree(c.scal);
     cudaFree(c.dres);
+    cudaFree(c.xr);
+    cudaFree(c.x0r);
     c = PrCache{};
 }
 
@@ -232,6 +234,28 @@ extern "C" int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float*
         }
         const int nblk = c.nblk;
         cudaStream_t s = c.s;
+        // SPMM_RELABEL: the iterations run on the ranks in the handle's vertex
+        // order, in a buffer the handle keeps (so the captured graph stays
+        // valid); the start vector comes in and the ranks go out once
+        float* const x_user = x;
+        if (A->relabel) {
+            if (!c.xr && (e = cudaMalloc((void**)&c.xr, (size_t)n * sizeof(float))) != cudaSuccess) {
+                fail(e, "spmm_pagerank: relabelled ranks");
+                break;
+            }
+            if (x0) {
+                if (!c.x0r && (e = cudaMalloc((void**)&c.x0r, (size_t)n * sizeof(float))) != cudaSuccess) {
+                    fail(e, "spmm_pagerank: relabelled start vector");
+                    break;
+                }
+                if ((e = relabel_rows_dev(A, x0, 1, 1, 4, c.x0r, 1, true, s)) != cudaSuccess) {
+                    fail(e, "spmm_pagerank: start vector into the handle's order");
+                    break;
+                }
+                x0 = c.x0r;
+            }
+            x = c.xr;
+        }
         // set-up outside the graph: 1/L, the start vector, z and its dangling mass
         pr_init_kernel<<<nblk, kPrThreads, 0, s>>>(A->fwd.row_ptr, n, c.inv_deg, x, x0);
         pr_scale_kernel<<<nblk, kPrThreads, 0, s>>>(x, c.inv_deg, n, c.z, c.part);
@@ -281,6 +305,10 @@ extern "C" int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float*
                 c.iters = iters;
             }
             if ((e = cudaGraphLaunch(c.exec, s)) != cudaSuccess) { fail(e, "spmm_pagerank: launch"); break; }
+        }
+        if (A->relabel && (e = relabel_rows_dev(A, x, 1, 1, 4, x_user, 1, false, s)) != cudaSuccess) {
+            fail(e, "spmm_pagerank: ranks into the input order");
+            break;
         }
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "spmm_pagerank: run"); break; }
         int32_t st = 0;

@@ -135,6 +135,10 @@ int check_common(const spmm_mat* A, spmm_dtype xtype, int32_t transpose, const c
         set_error(std::string(who) + ": 16-bit values need X of the same 16-bit type (or use F32 values)");
         return SPMM_ERR_UNSUPPORTED;
     }
+    if (A->relabel) {
+        set_error(std::string(who) + ": handles with SPMM_RELABEL take device buffers (spmm_apply)");
+        return SPMM_ERR_UNSUPPORTED;
+    }
     return SPMM_OK;
 }
 

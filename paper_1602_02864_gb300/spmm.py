@@ -26,6 +26,7 @@ SPMM_WANT_TRANSPOSE = 0x1
 SPMM_HOST_STREAMING = 0x2
 SPMM_REORDER = 0x4
 SPMM_FILE_DIRECT = 0x8
+SPMM_RELABEL = 0x10
 
 _STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_FORMAT", -5: "ERR_TIMEOUT",
            -6: "ERR_UNSUPPORTED", -7: "ERR_IO"}
@@ -53,7 +54,7 @@ class spmm_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("n_rows", "n_cols", "nnz", "n_tasks", "n_split_rows", "n_segments",
                                               "n_tasks_t", "n_split_rows_t", "n_segments_t", "device_bytes")] + [
         ("value_dtype", ctypes.c_int32), ("has_transpose", ctypes.c_int32), ("n_graphs", ctypes.c_int32),
-        ("reserved", ctypes.c_int32), ("walk_eff", ctypes.c_double * 4), ("walk_eff_t", ctypes.c_double * 4),
+        ("relabelled", ctypes.c_int32), ("walk_eff", ctypes.c_double * 4), ("walk_eff_t", ctypes.c_double * 4),
         ("n_hot", ctypes.c_int64), ("n_hot_t", ctypes.c_int64)]
 
 
@@ -121,6 +122,14 @@ _lib.spmm_write_csr_file.argtypes = [ctypes.c_char_p, _i64, _i64, _i64, _P, _P, 
 _lib.spmm_write_csr_file.restype = ctypes.c_int
 _lib.spmm_create_file.argtypes = [ctypes.POINTER(_P), ctypes.c_char_p, ctypes.c_uint32, _P, _P]
 _lib.spmm_create_file.restype = ctypes.c_int
+_lib.spmm_apply_relabelled.argtypes = [_P, _P, _i64, _i32, ctypes.c_int, _P, _i64, ctypes.c_int, _i32, _P]
+_lib.spmm_apply_relabelled.restype = ctypes.c_int
+_lib.spmm_relabel_rows.argtypes = [_P, _P, _i64, _i32, ctypes.c_int, _P, _i64, _i32, _P]
+_lib.spmm_relabel_rows.restype = ctypes.c_int
+_lib.spmm_get_relabel.argtypes = [_P, _P]
+_lib.spmm_get_relabel.restype = ctypes.c_int
+_lib.spmm_relabel_order.argtypes = [_i64, _P, _P, _P]
+_lib.spmm_relabel_order.restype = ctypes.c_int
 _lib.spmm_last_error.argtypes = []
 _lib.spmm_last_error.restype = ctypes.c_char_p
 
@@ -200,6 +209,42 @@ def spmm_create_csr(n_rows, n_cols, row_ptr, col_idx, values=None, flags=0, opts
 def spmm_apply(h, X, ldx, k, xtype, Y, ldy, transpose=0, stream=None):
     _check(_lib.spmm_apply(h, _ptr(X), int(ldx), int(k), int(xtype), _ptr(Y), int(ldy), SPMM_F32,
                            int(transpose), _stream_handle(stream)))
+
+
+def spmm_apply_relabelled(h, X, ldx, k, xtype, Y, ldy, transpose=0, stream=None):
+    """spmm_apply with X and Y in the handle's vertex order (SPMM_RELABEL)."""
+    _check(_lib.spmm_apply_relabelled(h, _ptr(X), int(ldx), int(k), int(xtype), _ptr(Y), int(ldy), SPMM_F32,
+                                      int(transpose), _stream_handle(stream)))
+
+
+def spmm_relabel_rows(h, src, dst, to_handle_order, stream=None):
+    """dst = src's rows in the handle's order (to_handle_order) or back in
+    the input order; src, dst 2-D CUDA tensors of one dtype, unit column
+    stride."""
+    if src.dim() != 2 or dst.dim() != 2 or src.stride(1) != 1 or dst.stride(1) != 1:
+        raise ValueError("src and dst must be 2-D with unit column stride")
+    if src.dtype != dst.dtype or src.shape != dst.shape:
+        raise ValueError("src and dst must have one dtype and shape")
+    _check(_lib.spmm_relabel_rows(h, _ptr(src), int(src.stride(0)), int(src.shape[1]), _torch_dtype_code(src),
+                                  _ptr(dst), int(dst.stride(0)), int(bool(to_handle_order)), _stream_handle(stream)))
+
+
+def spmm_get_relabel(h, n) -> np.ndarray:
+    """old_of_new of the handle (the identity without SPMM_RELABEL)."""
+    out = np.empty(int(n), dtype=np.int32)
+    _check(_lib.spmm_get_relabel(h, _P(out.ctypes.data)))
+    return out
+
+
+def spmm_relabel_order(n, row_ptr, col_idx) -> np.ndarray:
+    """Host-only: the vertex order SPMM_RELABEL gives an n x n CSR matrix
+    (old_of_new: decreasing row + column entry count, ties by vertex)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    out = np.empty(int(n), dtype=np.int32)
+    _check(_lib.spmm_relabel_order(int(n), _P(rp.ctypes.data), _P(ci.ctypes.data) if ci.size else None,
+                                   _P(out.ctypes.data)))
+    return out
 
 
 def spmm_apply_batched(handles, Xs, Ys, transpose=False, stream=None):
@@ -482,10 +527,10 @@ class SparseMatrix:
     """A sparse matrix resident in HBM: ``SparseMatrix(A_csr).apply(X)``."""
 
     def __init__(self, n_rows, n_cols, row_ptr, col_idx, values=None, transpose=False,
-                 opts: spmm_opts | None = None, stream=None, streaming=False, reorder=False):
+                 opts: spmm_opts | None = None, stream=None, streaming=False, reorder=False, relabel=False):
         self.n_rows, self.n_cols = int(n_rows), int(n_cols)
         flags = ((SPMM_WANT_TRANSPOSE if transpose else 0) | (SPMM_HOST_STREAMING if streaming else 0)
-                 | (SPMM_REORDER if reorder else 0))
+                 | (SPMM_REORDER if reorder else 0) | (SPMM_RELABEL if relabel else 0))
         if streaming:
             # the library borrows these host arrays until close(): keep them alive
             self._borrowed = (np.ascontiguousarray(row_ptr, dtype=np.int64),
@@ -513,12 +558,13 @@ class SparseMatrix:
 
     @classmethod
     def batched(cls, graphs, transpose=False, weighted=True, opts: spmm_opts | None = None, stream=None,
-                reorder=False):
+                reorder=False, relabel=False):
         """Block-diagonal handle over a list of graphs (one launch per apply)."""
         self = cls.__new__(cls)
         self.n_rows = int(sum(g.n_rows for g in graphs))
         self.n_cols = int(sum(g.n_cols for g in graphs))
-        flags = (SPMM_WANT_TRANSPOSE if transpose else 0) | (SPMM_REORDER if reorder else 0)
+        flags = ((SPMM_WANT_TRANSPOSE if transpose else 0) | (SPMM_REORDER if reorder else 0)
+                 | (SPMM_RELABEL if relabel else 0))
         self.handle = spmm_create_batched(graphs, flags, opts, stream, weighted)
         return self
 
@@ -566,6 +612,39 @@ class SparseMatrix:
             raise ValueError("Y must be a 2-D float32 tensor with unit column stride")
         spmm_apply(self.handle, X, X.stride(0), k, _torch_dtype_code(X), Y, Y.stride(0), int(transpose), stream)
         return Y
+
+    def apply_relabelled(self, X, transpose=False, Y=None, stream=None):
+        """apply() with X and Y in the handle's vertex order (SPMM_RELABEL)."""
+        import torch
+        if X.dim() != 2 or X.stride(1) != 1:
+            raise ValueError("X must be 2-D with unit column stride")
+        k = X.shape[1]
+        out_rows = self.n_cols if transpose else self.n_rows
+        if Y is None:
+            Y = torch.empty((out_rows, k), dtype=torch.float32, device=X.device)
+        if Y.dim() != 2 or Y.stride(1) != 1 or Y.dtype != torch.float32:
+            raise ValueError("Y must be a 2-D float32 tensor with unit column stride")
+        spmm_apply_relabelled(self.handle, X, X.stride(0), k, _torch_dtype_code(X), Y, Y.stride(0), int(transpose),
+                              stream)
+        return Y
+
+    def to_handle_order(self, M, out=None, stream=None):
+        """M's rows (input vertex order) in the handle's order."""
+        import torch
+        out = torch.empty_like(M) if out is None else out
+        spmm_relabel_rows(self.handle, M, out, True, stream)
+        return out
+
+    def to_input_order(self, M, out=None, stream=None):
+        """M's rows (handle's vertex order) back in the input order."""
+        import torch
+        out = torch.empty_like(M) if out is None else out
+        spmm_relabel_rows(self.handle, M, out, False, stream)
+        return out
+
+    def vertex_order(self) -> np.ndarray:
+        """old_of_new: the input vertex that is each vertex of the handle."""
+        return spmm_get_relabel(self.handle, self.n_rows)
 
     def info(self) -> dict:
         return spmm_get_info(self.handle)

@@ -192,7 +192,10 @@ typedef struct {
  * vertex order, spmm_relabel_order), and each row of B keeps its entries in
  * increasing new column order.  The most-gathered rows of X then share L2
  * lines and each warp task gathers from a narrower band of X (R-MAT scale 24:
- * 8-25% faster from k = 2 on, with the vectors in the new order).  Vectors in
+ * 8-33% faster from k = 2 on, with the vectors in the new order).  Graphs
+ * whose locality comes from clusters of similar degree rather than from hubs
+ * lose it (a clustered block model ran 0.5-0.8x as fast at k = 8), so the flag
+ * suits skewed degree distributions.  Vectors in
  * the new order ("the handle's order") go to spmm_apply_relabelled at no
  * extra cost; spmm_apply keeps the input order by gathering X's rows into the
  * handle's order and Y's rows back (two buffers the handle keeps and grows,

@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--record-traffic", default=None, metavar="CSV",
                     help="write the traffic record from an ncu raw CSV export of one rows_kernel launch, then exit")
     ap.add_argument("--pagerank-iters", type=int, default=30)
+    ap.add_argument("--profile-part", default="steps", choices=["steps", "relabelled"],
+                    help="what a profiler started with --profile-from-start off records: the timed steps, "
+                         "or one product per k on the relabelled handle")
     ap.add_argument("--no-relabel", action="store_true",
                     help="skip the sub-record of the same sweep on a handle made with SPMM_RELABEL")
     ap.add_argument("--no-configs", action="store_true",
@@ -969,8 +972,9 @@ def main():
     peak_gbs, peak_kind = load_peaks()
     with ClockSampler(local) as clk:
         barrier()
-        # a profiler started with --profile-from-start off records only these steps
-        profiler_range(True)
+        # a profiler started with --profile-from-start off records only these
+        # steps (or, with --profile-part relabelled, only the relabelled products)
+        profiler_range(args.profile_part == "steps")
         for _ in range(args.steps):
             flush.zero_()
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -1136,6 +1140,11 @@ def main():
         for k in ks:
             Xr = hr.to_handle_order(X[k])
             Yr = torch.empty((N, k), dtype=torch.float32, device=dev)
+            hr.apply_relabelled(Xr, Y=Yr)
+            flush.zero_()
+            profiler_range(args.profile_part == "relabelled")
+            hr.apply_relabelled(Xr, Y=Yr)
+            profiler_range(False)
             ms = event_ms(lambda: hr.apply_relabelled(Xr, Y=Yr), args.steps, flush)
             B = alg_bytes(nnz, N, N, k, 4)
             d = (hr.to_input_order(Yr) - Y[k]).abs().max().item() / max(Y[k].abs().max().item(), 1e-30)

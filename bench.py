@@ -940,10 +940,15 @@ def main():
     Y = {k: torch.empty((N, k), dtype=torch.float32, device=dev) for k in ks}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    # per product: the task kernel, the combine pass (if rows are split) and,
+    # for 4-byte X rows (k = 1 float32), the packing of the hot X rows
     launches_per_apply = 1 + (1 if info["n_split_rows"] > 0 else 0)
-    # per PageRank call: init, scale, reduce, then per iteration the task
-    # kernel, the combine pass (if rows are split), the update and the reduce
-    launches_per_pr_iter = 3 + (1 if info["n_split_rows_t"] > 0 else 0)
+    sweep_launches = sum(launches_per_apply + (1 if k == 1 and info["n_hot"] > 0 else 0) for k in ks)
+    # per PageRank call: init, scale, reduce, then per iteration the hot-row
+    # packing, the task kernel, the combine pass (if rows are split), the
+    # update and the reduce
+    launches_per_pr_iter = (3 + (1 if info["n_split_rows_t"] > 0 else 0)
+                            + (1 if info["n_hot_t"] > 0 else 0))
     xpr = torch.empty(N, dtype=torch.float32, device=dev)
     pr_res = [None]
 
@@ -1268,7 +1273,7 @@ def main():
             "configs": configs,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
-            "gpu_launches": (launches_per_apply * len(ks) + launches_per_pr_iter * args.pagerank_iters
+            "gpu_launches": (sweep_launches + launches_per_pr_iter * args.pagerank_iters
                              + (3 if args.pagerank_iters else 0)) * args.steps,
             "setup_s": {"generate": round(t_gen, 2), "create": round(t_create, 2), "autotune": round(t_tune, 2)},
             "autotuned_plan": tuned,

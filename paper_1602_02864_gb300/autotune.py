@@ -66,3 +66,34 @@ def tune(matrix, k, xtype=_sp.SPMM_F32, transpose=False, cache_path: str | None 
         cache[key] = choice
         _save(cache_path, cache)
     return dict(choice, cached=False)
+
+
+def tune_batched(matrices, Xs, Ys, candidates=None, reps=5, transpose=False) -> dict:
+    """Put every matrix of a spmm_apply_batched call on the one plan that
+    makes the whole batched call fastest.  A plan timed on one small graph
+    alone measures launch latency, not its share of a shared launch, so the
+    batch is timed as a whole: each candidate is applied to every handle
+    (spmm_replan), the batched call runs once to warm up and `reps` times
+    under CUDA events, and the handles are left on the fastest.  Returns the
+    chosen knobs with "ms" and the time of every candidate."""
+    import torch
+    cands = list(candidates) if candidates is not None else list(_sp.BUILTIN_GRID)
+    handles = [m.handle for m in matrices]
+    times = []
+    for c in cands:
+        o = _sp.spmm_opts(**c)
+        for h in handles:
+            _sp.spmm_replan(h, o, int(transpose))
+        _sp.spmm_apply_batched(handles, Xs, Ys, transpose)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            _sp.spmm_apply_batched(handles, Xs, Ys, transpose)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / reps)
+    best = min(range(len(cands)), key=lambda i: times[i])
+    o = _sp.spmm_opts(**cands[best])
+    for h in handles:
+        _sp.spmm_replan(h, o, int(transpose))
+    return dict(cands[best], ms=times[best], candidate_ms=times)

@@ -36,3 +36,33 @@ def test_autotune_picks_a_candidate_and_stays_exact(tmp_path):
     assert {n: c2[n] for n in cands[0]} == {n: c1[n] for n in cands[0]}
     h.sync_status()
     h.close()
+
+
+def test_tune_batched_leaves_every_handle_on_one_plan_and_exact():
+    """The batch-level tuner times the batched call for each candidate, leaves
+    every handle on the fastest, and the batched results stay exact."""
+    import torch
+    from paper_1602_02864_gb300 import autotune, spmm as sp
+    graphs = [synth.chunglu_csr(g, seed=0, nmin=1000, nmax=20000) for g in range(6)]
+    hs = [sp.SparseMatrix(g.n_rows, g.n_cols, g.row_ptr, g.col_idx, None) for g in graphs]
+    try:
+        ks = [1, 8, 16, 8, 33, 4]
+        Xh = [synth.dense(g.n_cols, k, seed=i, mode="int") for i, (g, k) in enumerate(zip(graphs, ks))]
+        Xs = [torch.from_numpy(x).cuda() for x in Xh]
+        Ys = [torch.empty((g.n_rows, k), device="cuda") for g, k in zip(graphs, ks)]
+        cands = [dict(task_nnz=128, short_max=15, long_row=512), dict(task_nnz=512, short_max=63, long_row=512),
+                 dict(task_nnz=256, short_max=31, long_row=256, x_l2_policy=1)]
+        r = autotune.tune_batched(hs, Xs, Ys, candidates=cands, reps=2)
+        assert len(r["candidate_ms"]) == 3 and r["ms"] == min(r["candidate_ms"])
+        chosen = {n: r[n] for n in cands[0]}
+        assert chosen in [{n: c[n] for n in cands[0]} for c in cands]
+        for g, h in zip(graphs, hs):
+            tasks, _, _ = sp.spmm_plan_tasks(g.row_ptr, sp.spmm_opts(**chosen))
+            assert h.info()["n_tasks"] == len(tasks) - 1
+        sp.spmm_apply_batched([h.handle for h in hs], Xs, Ys)
+        for g, x, y in zip(graphs, Xh, Ys):
+            ref = oracle.spmm(g.n_rows, g.n_cols, g.row_ptr, g.col_idx, None, x)
+            assert np.array_equal(y.cpu().numpy().astype(np.float64), ref)
+    finally:
+        for h in hs:
+            h.close()

@@ -743,7 +743,10 @@ def workload_nmf_batched(args, nmf_ks=(8, 16, 32)):
     apply_batched["k16_autotuned_batch"] = {
         "ms": ms_b2, "speedup_vs_default_plans": ms_q / ms_b2, "autotune_s": round(t_tb, 2),
         "plan": {n: tb[n] for n in ("task_nnz", "short_max", "long_row", "x_l2_policy")},
-        "candidates": len(tb["candidate_ms"]), "max_normwise_diff_vs_default_plans": normwise(Yq, Ys)}
+        "candidates": len(tb["candidate_ms"]),
+        "candidate_ms_min_median_max": [float(np.min(tb["candidate_ms"])), float(np.median(tb["candidate_ms"])),
+                                        float(np.max(tb["candidate_ms"]))],
+        "max_normwise_diff_vs_default_plans": normwise(Yq, Ys)}
     for s_ in singles:
         s_.close()
     nmf = {}

@@ -200,3 +200,37 @@ def test_unsupported_combinations(sp, rmat14, hp):
     with pytest.raises(sp.SpmmError) as e:
         sp.SparseMatrix.batched([A, A], relabel=True)
     assert e.value.status == sp.SPMM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("case", ["one_vertex_empty", "empty_5", "loops_and_isolated", "ragged_small"])
+def test_degenerate_matrices(sp, case):
+    """Tiny and degenerate square matrices through every entry point that
+    takes vectors: results in the input order equal the oracle's exactly."""
+    import torch
+    from tests import graphs
+    if case == "one_vertex_empty":
+        n, rp, ci = 1, np.array([0, 0]), np.zeros(0, np.int32)
+    elif case == "empty_5":
+        n, rp, ci = 5, np.zeros(6, np.int64), np.zeros(0, np.int32)
+    elif case == "loops_and_isolated":
+        n, rp, ci = 6, np.array([0, 1, 1, 3, 3, 4, 4]), np.array([0, 2, 5, 4], np.int32)
+    else:
+        A = synth.rmat_csr(7, seed=11)
+        n, rp, ci = A.n_rows, A.row_ptr, A.col_idx
+    rp = np.asarray(rp, np.int64)
+    h = sp.SparseMatrix(n, n, rp, ci, None, transpose=True, relabel=True)
+    try:
+        np.testing.assert_array_equal(h.vertex_order(), sp.spmm_relabel_order(n, rp, ci))
+        for k in (1, 3, 64):
+            X = synth.dense(n, k, seed=k, mode="int")
+            for tr in (False, True):
+                Y = h.apply(to_dev(X), transpose=tr).cpu().numpy().astype(np.float64)
+                assert np.array_equal(Y, oracle.spmm(n, n, rp, ci, None, X, transpose=tr)), (case, k, tr)
+                Yr = h.to_input_order(h.apply_relabelled(h.to_handle_order(to_dev(X)), transpose=tr))
+                assert np.array_equal(Yr.cpu().numpy().astype(np.float64), Y)
+        if rp[-1] > 0:
+            x, _ = h.pagerank(0.85, 5)
+            xr, _ = oracle.pagerank(n, rp, ci, 0.85, 5)
+            assert np.all(np.abs(x.cpu().numpy() - xr) <= 1e-5 * xr + 1e-12)
+    finally:
+        h.close()

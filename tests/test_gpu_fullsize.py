@@ -94,6 +94,42 @@ def test_rmat24_pagerank_30_iterations(sp, rmat24):
     h.close()
 
 
+def test_rmat24_relabelled_sweep_and_pagerank(sp, rmat24):
+    """The relabelled handle the bench's `relabelled` record times (SPMM_RELABEL,
+    products with the vectors in the handle's order): sampled rows of every k
+    against the oracle, integer X exact, and 30 PageRank iterations through the
+    public call against the oracle's ranks."""
+    import torch
+    A = rmat24
+    N = A.n_rows
+    h = sp.SparseMatrix(N, N, A.row_ptr, A.col_idx, None, transpose=True, relabel=True)
+    try:
+        o = torch.from_numpy(h.vertex_order().astype(np.int64))
+        new_of_old = torch.empty_like(o)
+        new_of_old[o] = torch.arange(N)
+        Xh = synth.dense(N, 64, seed=0)
+        X = torch.from_numpy(Xh).cuda()
+        rows = np.unique(synth.sample_rows(N, 3000, seed=12))
+        rt = new_of_old[torch.from_numpy(rows)].cuda()      # where the sampled rows sit in the handle's order
+        th = oracle.num_threads()
+        ref = oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xh, rows, threads=th)
+        scale = oracle.spmm_rows(A.row_ptr, A.col_idx, None, np.abs(Xh), rows, threads=th)
+        for k in KS:
+            Xr = h.to_handle_order(X[:, :k].contiguous())
+            Yr = h.apply_relabelled(Xr)
+            assert_close_rel(Yr[rt].cpu().numpy(), ref[:, :k], scale[:, :k], 1e-5, what=f"relabelled k={k}")
+        Xi = synth.dense(N, 8, seed=5, mode="int")
+        ref_i = oracle.spmm_rows(A.row_ptr, A.col_idx, None, Xi, rows, threads=th)
+        Yi = h.apply(torch.from_numpy(Xi).cuda())                                  # input order
+        assert np.array_equal(Yi[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64), ref_i)
+        x, _ = h.pagerank(0.85, 30)
+        xr, _ = oracle.pagerank(N, A.row_ptr, A.col_idx, 0.85, 30)
+        xg = x.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(xg - xr) <= 1e-5 * xr + 1e-12), np.max(np.abs(xg - xr) / xr)
+    finally:
+        h.close()
+
+
 def test_sym_rmat25_lcc_spmm_and_eigensolver(sp):
     """The eigensolver configuration at scale 25: the block product S V at
     k = 16 (FP32 and BF16 X) on sampled rows, then a few restarts of the

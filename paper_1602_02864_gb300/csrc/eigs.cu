@@ -7,10 +7,13 @@
 // expansion multiplies the newest block by S through the task kernel (X =
 // the block in FP32 or BF16, FP32 accumulation, converted back to FP64);
 // orthogonalisation is block classical Gram-Schmidt applied twice followed by
-// CholQR2, all in FP64; the Rayleigh-Ritz problem T = V^T (S V) is solved on
-// the host in FP64 by cyclic Jacobi; a restart keeps the best nev + block Ritz
-// vectors and their images, and the next expansion starts from S applied to
-// the kept Ritz vectors (whose components orthogonal to V are the residuals).
+// CholQR2, all in FP64 and on the device (the b x b Cholesky factor and its
+// inverse by one small kernel), so the expansions of a cycle are captured as
+// one CUDA graph; the Rayleigh-Ritz problem T = V^T (S V) is solved on the
+// host in FP64 by cyclic Jacobi once per restart; a restart keeps the best
+// nev + block Ritz vectors and their images, and the next expansion starts
+// from S applied to the kept Ritz vectors (whose components orthogonal to V
+// are the residuals).
 //
 // Tall-skinny FP64 kernels: C = A^T B (chunked partials added in a fixed
 // order) and Out = beta Out + alpha A C (one thread per output element).
@@ -138,6 +141,57 @@ __global__ void f32_to_bf16_kernel(const float* __restrict__ src, int64_t total,
         dst[t] = __float2bfloat16(src[t]);
 }
 
+// Block Cholesky G = R^T R (R upper, b x b row-major, b <= 32) and its inverse
+// Rinv = R^-1 (upper), by one block of 32 threads: the pivots in turn (thread
+// 0), each pivot's row of R across the threads, then column c of the inverse
+// by back substitution in thread c.  A pivot that is not safely positive
+// (below 1e-24 x trace) marks *flag and leaves the identity in Rinv, so the
+// kernels queued after it keep running on finite numbers until the host
+// reads the flag.
+__global__ void chol_inv_kernel(const double* __restrict__ G, int b, double* __restrict__ Rinv,
+                                int32_t* __restrict__ flag) {
+    __shared__ double R[32 * 32];
+    __shared__ int bad;
+    const int t = threadIdx.x;
+    if (t == 0) bad = 0;
+    for (int e = t; e < b * b; e += blockDim.x) R[e] = 0.0;
+    __syncthreads();
+    double tr = 0.0;
+    for (int i = 0; i < b; ++i) tr += G[i * b + i];
+    for (int j = 0; j < b; ++j) {
+        if (t == 0) {
+            double d = G[j * b + j];
+            for (int k = 0; k < j; ++k) d -= R[k * b + j] * R[k * b + j];
+            if (!(d > 1e-24 * (tr > 0 ? tr : 1.0))) bad = 1;
+            R[j * b + j] = bad ? 1.0 : sqrt(d);
+        }
+        __syncthreads();
+        if (bad) break;
+        const double rjj = R[j * b + j];
+        for (int i = j + 1 + t; i < b; i += blockDim.x) {
+            double s = G[j * b + i];
+            for (int k = 0; k < j; ++k) s -= R[k * b + j] * R[k * b + i];
+            R[j * b + i] = s / rjj;
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        for (int e = t; e < b * b; e += blockDim.x) Rinv[e] = (e / b == e % b) ? 1.0 : 0.0;
+        if (t == 0) *flag = 1;
+        return;
+    }
+    for (int c = t; c < b; c += blockDim.x) {
+        double x[32];
+        x[c] = 1.0 / R[c * b + c];
+        for (int i = c - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int k = i + 1; k <= c; ++k) s += R[i * b + k] * x[k];
+            x[i] = -s / R[i * b + i];
+        }
+        for (int i = 0; i < b; ++i) Rinv[i * b + c] = i <= c ? x[i] : 0.0;
+    }
+}
+
 // ---------------------------------------------------------------- host linear algebra
 // Cholesky G = R^T R (R upper); false if a pivot is not safely positive.
 static bool cholesky_upper(int b, const std::vector<double>& G, std::vector<double>& R) {
@@ -227,6 +281,8 @@ struct Eig {
     cudaStream_t s;
     double *V = nullptr, *AV = nullptr, *W = nullptr, *W2 = nullptr, *part = nullptr, *small = nullptr;
     double *U = nullptr, *AU = nullptr, *theta = nullptr;
+    double* small2 = nullptr;   // b x b inverse Cholesky factor (device-side CholQR)
+    int32_t* flags = nullptr;   // breakdown flag of each expansion of a cycle (device)
     float* Yf = nullptr;
     void* Xs = nullptr;
     int64_t chunk = 0;
@@ -262,6 +318,51 @@ struct Eig {
         if (rc != SPMM_OK) return rc;
         f32_to_f64_kernel<<<grid, kEigThreads, 0, s>>>(Yf, b, n, out, ldo);
         return SPMM_OK;
+    }
+    // C = A^T B into device memory, and Out = beta Out + alpha A C with C in
+    // device memory: the tall-skinny products with no host round trip
+    void tn_dev(const double* Am, int64_t lda, int p, const double* Bm, int64_t ldb, int q, double* out) {
+        ts_tn_partial_kernel<<<nchunks, kEigThreads, 0, s>>>(Am, lda, p, Bm, ldb, q, n, chunk, part);
+        ts_reduce_kernel<<<(p * q + 255) / 256, 256, 0, s>>>(part, nchunks, p * q, out);
+    }
+    void nn_dev(const double* Am, int64_t lda, int p, const double* C, int q, double* Out, int64_t ldo, double alpha,
+                double beta) {
+        ts_nn_kernel<<<grid, kEigThreads, 0, s>>>(Am, lda, p, C, q, Out, ldo, n, alpha, beta);
+    }
+    // orthonormalise() on the device only: CGS2 against V[:, :cur], then
+    // CholQR2 with the Cholesky factor inverted by chol_inv_kernel; a
+    // breakdown marks flags[slot] instead of returning
+    void orthonormalize_dev(int cur, int slot) {
+        for (int pass = 0; pass < 2 && cur > 0; ++pass) {
+            tn_dev(V, m, cur, W, b, b, small);
+            nn_dev(V, m, cur, small, b, W, b, -1.0, 1.0);
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+            tn_dev(W, b, b, W, b, b, small);
+            chol_inv_kernel<<<1, 32, 0, s>>>(small, b, small2, flags + slot);
+            nn_dev(W, b, b, small2, b, W2, b, 1.0, 0.0);
+            std::swap(W, W2);
+        }
+    }
+    // n_exp expansions of the basis from column cur0, the first from the
+    // image AV[:, seed0] and each next one from the image of the block before;
+    // every step stays on the device (a breakdown in expansion x marks
+    // flags[x]), so a cycle can be captured as one graph
+    int expand_cycle(int cur0, int seed0, int n_exp) {
+        cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)n_exp * sizeof(int32_t), s);
+        if (e != cudaSuccess) return cuda_fail(e, "spmm_eigs: flags");
+        int cur = cur0, seed = seed0;
+        for (int x = 0; x < n_exp; ++x) {
+            copy_block_kernel<<<grid, kEigThreads, 0, s>>>(AV + seed, m, b, n, W, b);
+            orthonormalize_dev(cur, x);
+            copy_block_kernel<<<grid, kEigThreads, 0, s>>>(W, b, b, n, V + cur, m);
+            const int rc = apply_block(V + cur, m, AV + cur, m);
+            if (rc != SPMM_OK) return rc;
+            seed = cur;
+            cur += b;
+        }
+        e = cudaGetLastError();
+        return e == cudaSuccess ? SPMM_OK : cuda_fail(e, "spmm_eigs: expansion");
     }
     // orthonormalise W (n x b) against V[:, :cur] twice, then CholQR2; false on breakdown
     bool orthonormalize(int cur, cudaError_t& e) {
@@ -334,6 +435,8 @@ static int eigs_impl(spmm_mat_t S, int op, int32_t nev, int32_t block, int32_t m
             (e = cudaMalloc((void**)&E.W2, (size_t)n * m * sizeof(double))) != cudaSuccess ||
             (e = cudaMalloc((void**)&E.part, (size_t)E.nchunks * m * m * sizeof(double))) != cudaSuccess ||
             (e = cudaMalloc((void**)&E.small, (size_t)m * m * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.small2, (size_t)b * b * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&E.flags, (size_t)kEigMaxBasis * sizeof(int32_t))) != cudaSuccess ||
             (e = cudaMalloc((void**)&E.theta, (size_t)m * sizeof(double))) != cudaSuccess ||
             (e = cudaMalloc((void**)&E.Yf, (size_t)n * b * sizeof(float))) != cudaSuccess ||
             (e = cudaMalloc(&E.Xs, (size_t)n * b * sizeof(float))) != cudaSuccess ||
@@ -354,18 +457,56 @@ static int eigs_impl(spmm_mat_t S, int op, int32_t nev, int32_t block, int32_t m
         int cur = b, seed = 0, restarts = 0;
         std::vector<double> T, th, Y, Rn;
         bool done = false;
+        // Every cycle after the first restart expands the same columns from
+        // the same seeds, so that expansion phase is captured as one CUDA
+        // graph the second time it comes (the first run happens eagerly, so
+        // any buffer the product grows is grown outside the capture).
+        int g_cur0 = -1, g_n = -1, seen_cur0 = -1, seen_n = -1;
+        cudaGraphExec_t gexec = nullptr;
+        std::vector<int32_t> hflags(kEigMaxBasis);
         while (!done) {
-            // ---- expand the basis block by block
-            while (cur + b <= m) {
-                copy_block_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.AV + seed, m, b, n, E.W, b);
-                if (!E.orthonormalize(cur, e)) break;          // breakdown: the span is invariant
-                copy_block_kernel<<<E.grid, kEigThreads, 0, E.s>>>(E.W, b, b, n, E.V + cur, m);
-                if ((rc = E.apply_block(E.V + cur, m, E.AV + cur, m)) != SPMM_OK) break;
-                seed = cur;
-                cur += b;
+            // ---- expand the basis block by block (device only)
+            const int cur0 = cur, n_exp = (m - cur) / b;
+            if (n_exp > 0) {
+                if (gexec && g_cur0 == cur0 && g_n == n_exp && seed == 0) {
+                    if ((e = cudaGraphLaunch(gexec, E.s)) != cudaSuccess) { fail(e, "spmm_eigs: expansion graph"); break; }
+                } else if (seed == 0 && seen_cur0 == cur0 && seen_n == n_exp) {
+                    if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+                    if ((e = cudaStreamBeginCapture(E.s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+                        fail(e, "spmm_eigs: capture");
+                        break;
+                    }
+                    rc = E.expand_cycle(cur0, 0, n_exp);
+                    cudaGraph_t graph = nullptr;
+                    const cudaError_t ec = cudaStreamEndCapture(E.s, &graph);
+                    if (rc == SPMM_OK && ec != cudaSuccess) fail(ec, "spmm_eigs: end capture");
+                    if (rc == SPMM_OK && (e = cudaGraphInstantiate(&gexec, graph, 0)) != cudaSuccess) {
+                        gexec = nullptr;
+                        fail(e, "spmm_eigs: instantiate");
+                    }
+                    if (graph) cudaGraphDestroy(graph);
+                    if (rc != SPMM_OK) break;
+                    g_cur0 = cur0;
+                    g_n = n_exp;
+                    if ((e = cudaGraphLaunch(gexec, E.s)) != cudaSuccess) { fail(e, "spmm_eigs: expansion graph"); break; }
+                } else {
+                    if ((rc = E.expand_cycle(cur0, seed, n_exp)) != SPMM_OK) break;
+                    if (seed == 0) {
+                        seen_cur0 = cur0;
+                        seen_n = n_exp;
+                    }
+                }
+                // the first expansion that broke down (its span was invariant) ends the basis
+                if ((e = cudaMemcpyAsync(hflags.data(), E.flags, (size_t)n_exp * sizeof(int32_t),
+                                         cudaMemcpyDeviceToHost, E.s)) != cudaSuccess ||
+                    (e = cudaStreamSynchronize(E.s)) != cudaSuccess) {
+                    fail(e, "spmm_eigs: expansion flags");
+                    break;
+                }
+                int x = 0;
+                while (x < n_exp && hflags[(size_t)x] == 0) ++x;
+                cur = cur0 + x * b;
             }
-            if (rc != SPMM_OK) break;
-            if (e != cudaSuccess) { fail(e, "spmm_eigs: expand"); break; }
             // ---- Rayleigh-Ritz on span(V[:, :cur])
             if ((e = E.tn(E.V, m, cur, E.AV, m, cur, T)) != cudaSuccess) { fail(e, "spmm_eigs: projection"); break; }
             for (int i = 0; i < cur; ++i)
@@ -412,6 +553,7 @@ static int eigs_impl(spmm_mat_t S, int op, int32_t nev, int32_t block, int32_t m
             seed = 0;
             ++restarts;
         }
+        if (gexec) cudaGraphExecDestroy(gexec);
         if (rc != SPMM_OK) break;
         if ((e = cudaStreamSynchronize(E.s)) != cudaSuccess) { fail(e, "spmm_eigs: run"); break; }
         int32_t st = 0;
@@ -431,6 +573,7 @@ static int eigs_impl(spmm_mat_t S, int op, int32_t nev, int32_t block, int32_t m
     }
     cudaFree(E.V); cudaFree(E.AV); cudaFree(E.U); cudaFree(E.AU); cudaFree(E.W); cudaFree(E.W2);
     cudaFree(E.part); cudaFree(E.small); cudaFree(E.theta); cudaFree(E.Yf); cudaFree(E.Xs); cudaFree(E.T1);
+    cudaFree(E.small2); cudaFree(E.flags);
     return rc;
 }
 

@@ -192,16 +192,16 @@ def test_krylov_on_invariant_subspace(sp, values, block, nev):
     invariant after a few expansions.  Whatever the device-side expansions do
     beyond it (a CholQR2 breakdown that ends the basis, or rounding noise
     orthonormalised into new directions), the Ritz values are the exact top
-    eigenvalue (1, of multiplicity >= nev) with zero residual, at the first
-    Rayleigh-Ritz step."""
+    eigenvalue (1, of multiplicity >= nev) at the first Rayleigh-Ritz step,
+    with residuals at the rounding level of the FP32 products (~1e-8)."""
     n = 60
     d = np.array([values[i % len(values)] for i in range(n)])
     C = graphs.csr_from_edges(n, n, np.arange(n), np.arange(n), d)
     h = sp.SparseMatrix.from_csr(C)
     try:
         ev, res, nrest = h.eigs(nev, start_block(n, block, seed=3), block=block, max_basis=4 * block + nev,
-                                max_restarts=5, tol=1e-8)
+                                max_restarts=5, tol=1e-6)
         np.testing.assert_allclose(ev, np.ones(nev), atol=1e-7)
-        assert np.all(res <= 1e-8) and nrest == 0, (res, nrest)
+        assert np.all(res <= 1e-6) and nrest == 0, (res, nrest)
     finally:
         h.close()

@@ -184,7 +184,9 @@ typedef struct {
  * results are bit-identical to a handle without the flag given the same X as
  * a contiguous (ldx = k), 16-byte-aligned array -- the layout of the
  * relabelled copy.  A strided or misaligned X can give another summation
- * order (the kernel's vector width follows X's alignment).
+ * order (the kernel's vector width follows X's alignment).  spmm_apply calls
+ * on one SPMM_REORDER handle share its relabelled-X buffer and must not
+ * overlap (on several streams at once).
  *
  * SPMM_RELABEL (Section 5.1 again, for square matrices): the handle stores
  * B = P A P^T, where P renumbers the vertices by decreasing total degree
@@ -199,7 +201,8 @@ typedef struct {
  * the new order ("the handle's order") go to spmm_apply_relabelled at no
  * extra cost; spmm_apply keeps the input order by gathering X's rows into the
  * handle's order and Y's rows back (two buffers the handle keeps and grows,
- * n * k elements each).  spmm_pagerank, spmm_eigs, spmm_eigs_filtered,
+ * n * k elements each; spmm_apply calls on one such handle share them and
+ * must not overlap, as with SPMM_REORDER's buffer).  spmm_pagerank, spmm_eigs, spmm_eigs_filtered,
  * spmm_svds and spmm_nmf take and return vectors in the input order and run
  * in the handle's order in between.  The new summation order within a row
  * gives other float32 roundings than a handle without the flag.  Not with

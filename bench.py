@@ -90,9 +90,36 @@ def metric_name(args):
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "traffic_rows_kernel_k1.json")
 
 
+def code_tokens(src: str) -> str:
+    """C/C++/CUDA source without its comments, each run of white space one
+    blank: what the compiler sees, so an edit to a comment or to the layout
+    leaves the digest unchanged."""
+    import re
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return re.sub(r"\s+", " ", "".join(out)).strip()
+
+
 def source_digest() -> str:
     """SHA-256 over the CUDA/C++ sources and the public header (file names
-    and contents, in name order)."""
+    and their code without comments, in name order)."""
     import hashlib
     h = hashlib.sha256()
     dirs = [os.path.join(ROOT, "paper_1602_02864_gb300", "csrc"), os.path.join(ROOT, "include")]
@@ -100,8 +127,8 @@ def source_digest() -> str:
         for fn in sorted(os.listdir(d)):
             if fn.endswith((".cu", ".cuh", ".h", ".cpp")):
                 h.update(fn.encode())
-                with open(os.path.join(d, fn), "rb") as f:
-                    h.update(f.read())
+                with open(os.path.join(d, fn), encoding="utf-8", errors="replace") as f:
+                    h.update(code_tokens(f.read()).encode())
     return h.hexdigest()
 
 

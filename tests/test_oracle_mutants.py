@@ -50,6 +50,25 @@ MUTANTS = {
     # the A^T A operator applies A twice instead of A then A^T
     "svd_operator": ("w[col_idx[p]] += vget(val, vtype, p) * t[i];", "w[i] += vget(val, vtype, p) * t[col_idx[p]];",
                      [apps.test_svds_vs_numpy_svd]),
+    # the sampled-rows product reads the output row's own X row
+    "rows_wrong_index": ("acc += vget(val, vtype, p) * xget(X, xtype, (int64_t)col_idx[p] * ldx + j);",
+                         "acc += vget(val, vtype, p) * xget(X, xtype, (int64_t)i * ldx + j);",
+                         [sp.test_sampled_rows_and_threads_agree]),
+    # the sampled transposed product gathers instead of scattering
+    "t_rows_transposed_operand": ("Y[s * k + j] += a * xget(X, xtype, i * ldx + j);",
+                                  "Y[s * k + j] += a * xget(X, xtype, (int64_t)col_idx[p] * ldx + j);",
+                                  [sp.test_sampled_rows_and_threads_agree]),
+    # PageRank's teleport term not divided by N
+    "pr_teleport_not_divided": ("double base = (1.0 - d) / (double)n + d * dangling / (double)n;",
+                                "double base = (1.0 - d) + d * dangling / (double)n;",
+                                [apps.test_pagerank_two_node_closed_form, apps.test_pagerank_sums_to_one_every_iteration]),
+    # NMF H update with an off-by-one numerator column
+    "nmf_h_numerator": ("Ht[c * k + r] *= AtW[c * k + r] / (den[r] + eps);",
+                        "Ht[c * k + r] *= AtW[c * k + (r + 1) % k] / (den[r] + eps);",
+                        [lambda: apps.test_nmf_vs_dense_updates(True)]),
+    # block Lanczos always expands the first block instead of the newest one
+    "lanczos_expands_first_block": ("Q + (size_t)(lo + c) * n,", "Q + (size_t)c * n,",
+                                    [apps.test_lanczos_vs_dense_eigh_on_rmat, apps.test_lanczos_cycle_closed_form]),
 }
 
 

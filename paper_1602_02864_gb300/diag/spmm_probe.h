@@ -1,8 +1,8 @@
-// spmm_probe.h -- gather-ceiling diagnostics, built as libspmm_probe.so
+// spmm_probe.h -- gather-rate diagnostics, built as libspmm_probe.so
 // beside libspmm.so (which it links against for the handle and its error
 // string).  Not part of the library's interface and not a paper operation:
-// they measure the rate of random row gathers that bounds the SpMM, for the
-// benchmark's reports.  Errors are reported like the library's
+// they measure the rate of random row gathers, the SpMM's dominant cost, as
+// reference rates for the benchmark's reports.  Errors are reported like the library's
 // (spmm_last_error).
 #pragma once
 
@@ -14,7 +14,7 @@ extern "C" {
 
 /*
  * spmm_probe_gather -- diagnostic: the measured rate of uniformly random row
- * gathers on this GPU, the practical ceiling of the SpMM's dominant cost
+ * gathers on this GPU, a reference rate for the SpMM's dominant cost
  * (one X row per nonzero).  Gathers rows of row_bytes (a power of two,
  * 4..256) at random row indices from a zero-filled table of table_bytes
  * (4 KiB .. 64 GiB; below the L2 size the rows come from L2, above it from
@@ -26,7 +26,7 @@ int spmm_probe_gather(int64_t table_bytes, int32_t row_bytes, double* rows_per_s
                       void* stream);
 
 /*
- * spmm_probe_gather_cols -- diagnostic: the gather ceiling of one matrix.
+ * spmm_probe_gather_cols -- diagnostic: the gather rate of one matrix's column stream.
  * Replays the handle's own column-index stream (forward, or the transpose if
  * `transpose` != 0) in storage order, gathering for every stored entry one
  * row of row_bytes (a multiple of 4, 4..256; 4*k for an FP32 X of k columns)

@@ -1,5 +1,5 @@
 """ctypes binding of libspmm_probe.so (paper_1602_02864_gb300/diag/spmm_probe.h):
-the gather-ceiling diagnostics the benchmark reports beside the SpMM.  They
+the gather-rate diagnostics the benchmark reports beside the SpMM.  They
 are not part of the library's interface."""
 from __future__ import annotations
 

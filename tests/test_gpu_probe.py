@@ -1,4 +1,4 @@
-"""Gather-ceiling diagnostics: argument checks and sane magnitudes."""
+"""Gather-rate diagnostics: argument checks and sane magnitudes."""
 import pytest
 
 import synth

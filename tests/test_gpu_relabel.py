@@ -234,3 +234,63 @@ def test_degenerate_matrices(sp, case):
             assert np.all(np.abs(x.cpu().numpy() - xr) <= 1e-5 * xr + 1e-12)
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("vdtype", ["bfloat16", "float16"])
+@pytest.mark.parametrize("k", [1, 8, 64])
+def test_16bit_values(sp, rmat14w, vdtype, k):
+    """Stored 16-bit values move with their entries: X of the same type,
+    both orientations, against the oracle on the rounded inputs."""
+    import torch
+    A = rmat14w
+    vt = torch.from_numpy(A.values).to(getattr(torch, vdtype))
+    vr = vt.float().numpy().astype(np.float64)
+    h = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, vt, transpose=True, relabel=True)
+    try:
+        Xd = to_dev(synth.dense(A.n_cols, k, seed=4 + k), getattr(torch, vdtype))
+        Xr = rounded_host(Xd)
+        for tr in (False, True):
+            Y = h.apply(Xd, transpose=tr).cpu().numpy()
+            ref = oracle.spmm(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, vr, Xr, transpose=tr)
+            scale = oracle.spmm(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, np.abs(vr), np.abs(Xr), transpose=tr)
+            assert_close_rel(Y, ref, scale, 2e-3, f"relabel {vdtype} values k={k} t={tr}")
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("k", [1, 16])
+def test_compensated_plan(sp, rmat14w, k):
+    """Compensated sums for long rows and hub segments on the relabelled
+    matrix: the same parity, and the hub rows' partials still add up."""
+    A = rmat14w
+    o = sp.spmm_opts(compensated=1, long_row=64, task_nnz=64, short_max=15)
+    h = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.values, transpose=True, relabel=True, opts=o)
+    try:
+        assert h.info()["n_split_rows"] > 0
+        X = synth.dense(A.n_rows, k, seed=30 + k)
+        for tr in (False, True):
+            Y = h.apply(to_dev(X), transpose=tr).cpu().numpy()
+            ref = oracle.spmm(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.values, X, transpose=tr)
+            assert_close_rel(Y, ref, abs_product(A, X.astype(np.float64), tr), 1e-5, f"compensated k={k} t={tr}")
+    finally:
+        h.close()
+
+
+def test_relabelled_entry_strided_and_misaligned(sp, rmat14w, hw):
+    """spmm_apply_relabelled with X and Y as column windows of wider arrays
+    (leading dimension > k, X starting off a 16-byte boundary): the same
+    sums as on contiguous copies, within the FP32 tolerance."""
+    import torch
+    A = rmat14w
+    k = 5
+    Xw = to_dev(synth.dense(A.n_rows, k + 3, seed=8))
+    X = Xw[:, 1:1 + k]
+    Xr = torch.empty((A.n_rows, k + 3), device="cuda")[:, 2:2 + k]
+    sp.spmm_relabel_rows(hw.handle, X, Xr, True)
+    Yw = torch.full((A.n_rows, k + 4), 5.0, device="cuda")
+    hw.apply_relabelled(Xr, Y=Yw[:, :k])
+    Y = hw.to_input_order(Yw[:, :k].contiguous())
+    Xh = X.cpu().numpy().astype(np.float64)
+    ref = oracle.spmm(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.values, Xh)
+    assert_close_rel(Y.cpu().numpy(), ref, abs_product(A, Xh), 1e-5, "strided relabelled")
+    assert torch.all(Yw[:, k:] == 5.0)

@@ -149,6 +149,163 @@ __global__ void nmf_objective_kernel(const double* __restrict__ cross, const int
     }
 }
 
+// ---- ranks k = 8, 16, 32, 64 with 16-byte aligned factors: the same sums
+// organised for the memory system (the kernels above stage 32 or 16 rows at a
+// time behind block barriers and wait on every global load).
+
+// Gram partials, register-blocked: thread t owns the 4 x 4 block ob of the
+// K x K Gram (OB = (K/4)^2 blocks) and the rows rg, rg + RG, ... (RG =
+// 256 / OB row groups) of each tile of T = 4096 / K rows.  Tiles are staged
+// in shared memory from float4 loads issued one tile ahead (double buffer,
+// one barrier per tile); products are summed in FP32 over at most
+// kGramPromote rows per thread, then added to FP64; at the end the row
+// groups' FP64 blocks are added in row-group order behind one barrier.
+constexpr int kGramPromote = 128;
+
+template <int K>
+__global__ void __launch_bounds__(kNmfThreads, 3)
+gram_partial_blocked_kernel(const float* __restrict__ M, const int4* __restrict__ chunks,
+                            double* __restrict__ partial) {
+    constexpr int NB = K / 4, OB = NB * NB, RG = kNmfThreads / OB;
+    constexpr int T = 4096 / K;                    // rows per tile (4096 floats)
+    constexpr int TV = T * K / 4;                  // float4 per tile
+    constexpr int PV = TV / kNmfThreads;           // float4 per thread per tile
+    static_assert(TV % kNmfThreads == 0 && RG >= 1 && T % RG == 0, "tile shape");
+    __shared__ __align__(16) float tile[2][4096];
+    const int4 ch = chunks[blockIdx.x];
+    const int t = threadIdx.x, ob = t % OB, rg = t / OB;
+    const int rb = (ob / NB) * 4, sb = (ob % NB) * 4;
+    float a32[16];
+    double a64[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a32[j] = 0.f, a64[j] = 0.0;
+    int since = 0;
+    const int64_t r_begin = ch.y, r_end = ch.z;
+    const int64_t ntiles = (r_end - r_begin + T - 1) / T;
+    float4 pre[PV];
+    auto load = [&](int64_t ti) {
+        const int64_t r0 = r_begin + ti * T;
+        const int64_t nv = min((int64_t)T, r_end - r0) * (K / 4);   // float4 of real rows
+        const float4* src = reinterpret_cast<const float4*>(M + r0 * K);
+#pragma unroll
+        for (int p = 0; p < PV; ++p) {
+            const int v = t + p * kNmfThreads;
+            pre[p] = v < nv ? __ldg(src + v) : make_float4(0.f, 0.f, 0.f, 0.f);   // rows past the end add 0
+        }
+    };
+    if (ntiles > 0) load(0);
+    for (int64_t ti = 0; ti < ntiles; ++ti) {
+        float* tb = tile[ti & 1];
+#pragma unroll
+        for (int p = 0; p < PV; ++p) reinterpret_cast<float4*>(tb)[t + p * kNmfThreads] = pre[p];
+        __syncthreads();
+        if (ti + 1 < ntiles) load(ti + 1);
+        for (int r = rg; r < T; r += RG) {
+            const float4 x = *reinterpret_cast<const float4*>(tb + r * K + rb);
+            const float4 y = *reinterpret_cast<const float4*>(tb + r * K + sb);
+            const float xr[4] = {x.x, x.y, x.z, x.w}, yr[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a32[i * 4 + j] = fmaf(xr[i], yr[j], a32[i * 4 + j]);
+            if (++since == kGramPromote) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) a64[j] += (double)a32[j], a32[j] = 0.f;
+                since = 0;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a64[j] += (double)a32[j];
+    // every row group's FP64 block into shared memory (RG x K x K doubles =
+    // 32 KB, the tiles' space), then each element added over the row groups
+    // in row-group order
+    static_assert(RG * K * K * (int)sizeof(double) == (int)sizeof(tile), "row-group blocks fill the tiles' space");
+    double* red = reinterpret_cast<double*>(&tile[0][0]);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) red[rg * K * K + (rb + i) * K + sb + j] = a64[i * 4 + j];
+    __syncthreads();
+    for (int e = t; e < K * K; e += kNmfThreads) {
+        double sum = 0.0;
+        for (int g = 0; g < RG; ++g) sum += red[g * K * K + e];
+        partial[(int64_t)blockIdx.x * K * K + e] = sum;
+    }
+}
+
+// The update of nmf_update_kernel, warp by warp: a row sits on L = min(K, 32)
+// lanes (E = K / L elements each); den is formed with the row's elements
+// passed by shuffles, in the same order and the same FP32 operations as
+// nmf_update_kernel, four row groups in flight per warp; no block barrier
+// after the Gram is staged.
+template <int K>
+__global__ void __launch_bounds__(kNmfThreads)
+nmf_update_warp_kernel(float* __restrict__ M, const float* __restrict__ Num, const double* __restrict__ G,
+                       const int4* __restrict__ chunks, float eps) {
+    constexpr int L = K < 32 ? K : 32, E = K / L, RPW = 32 / L, U = 4;
+    __shared__ float g_s[K * K];
+    const int4 ch = chunks[blockIdx.x];
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) g_s[e] = (float)G[(int64_t)ch.x * K * K + e];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = lane / L, li = lane % L;
+    const int nw = blockDim.x >> 5;
+    for (int64_t base = ch.y + (int64_t)warp * RPW * U; base < ch.z; base += (int64_t)nw * RPW * U) {
+        float m[U][E], num[U][E];
+        bool on[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = base + u * RPW + sub;
+            on[u] = i < ch.z;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                m[u][e] = on[u] ? M[i * K + li + e * L] : 0.f;
+                num[u][e] = on[u] ? Num[i * K + li + e * L] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            float den[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) den[e] = 0.f;
+#pragma unroll
+            for (int e2 = 0; e2 < E; ++e2)
+                for (int q = 0; q < L; ++q) {
+                    const float mq = __shfl_sync(0xffffffffu, m[u][e2], q, L);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) den[e] = fmaf(mq, g_s[(q + e2 * L) * K + li + e * L], den[e]);
+                }
+            if (on[u]) {
+                const int64_t i = base + u * RPW + sub;
+#pragma unroll
+                for (int e = 0; e < E; ++e) M[i * K + li + e * L] = m[u][e] * (num[u][e] / (den[e] + eps));
+            }
+        }
+    }
+}
+
+// nmf_cross_kernel as one flat dot product over the chunk's elements (its rows
+// are contiguous): float4 loads, four products in FP32, FP64 per thread,
+// then the fixed-order block sum.
+__global__ void __launch_bounds__(kNmfThreads)
+nmf_cross_flat_kernel(const float* __restrict__ W, const float* __restrict__ AH, int k,
+                      const int4* __restrict__ chunks, double* __restrict__ partial) {
+    __shared__ double sh[32];
+    const int4 ch = chunks[blockIdx.x];
+    const int64_t e0 = (int64_t)ch.y * k, nv = ((int64_t)ch.z - ch.y) * k / 4;
+    const float4* w4 = reinterpret_cast<const float4*>(W + e0);
+    const float4* a4 = reinterpret_cast<const float4*>(AH + e0);
+    double acc = 0.0;
+#pragma unroll 4
+    for (int64_t v = threadIdx.x; v < nv; v += blockDim.x) {
+        const float4 w = __ldg(w4 + v), a = __ldg(a4 + v);
+        acc += (double)fmaf(w.w, a.w, fmaf(w.z, a.z, fmaf(w.y, a.y, w.x * a.x)));
+    }
+    const double s = nmf_block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
 __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
@@ -250,12 +407,32 @@ static int nmf_impl(spmm_mat_t A, int32_t k, int32_t steps, float* W, float* Ht,
             }
             return apply_dev(A, transpose, X, k, k, spmm_x, out, k, s);
         };
+        // ranks 8, 16, 32, 64 with 16-byte aligned factors take the blocked Gram,
+        // the warp-level update and the flat cross term
+        const bool blocked = (k == 8 || k == 16 || k == 32 || k == 64) && ((uintptr_t)W & 15) == 0 &&
+                             ((uintptr_t)Ht & 15) == 0;
         auto gram = [&](const float* M, bool wside, double* G) {
-            gram_partial_kernel<<<wside ? nbW : nbH, kNmfThreads, 0, s>>>(M, k, wside ? dchW : dchH, part);
+            const unsigned nb = wside ? nbW : nbH;
+            const int4* chs = wside ? dchW : dchH;
+            if (!blocked) gram_partial_kernel<<<nb, kNmfThreads, 0, s>>>(M, k, chs, part);
+            else if (k == 8) gram_partial_blocked_kernel<8><<<nb, kNmfThreads, 0, s>>>(M, chs, part);
+            else if (k == 16) gram_partial_blocked_kernel<16><<<nb, kNmfThreads, 0, s>>>(M, chs, part);
+            else if (k == 32) gram_partial_blocked_kernel<32><<<nb, kNmfThreads, 0, s>>>(M, chs, part);
+            else gram_partial_blocked_kernel<64><<<nb, kNmfThreads, 0, s>>>(M, chs, part);
             gram_reduce_kernel<<<ng, kNmfThreads, 0, s>>>(part, wside ? dgW : dgH, k, G);
         };
+        auto update = [&](float* M, const float* Num, const double* G, bool wside) {
+            const unsigned nb = wside ? nbW : nbH;
+            const int4* chs = wside ? dchW : dchH;
+            if (!blocked) nmf_update_kernel<<<nb, kNmfThreads, 0, s>>>(M, Num, G, k, chs, feps);
+            else if (k == 8) nmf_update_warp_kernel<8><<<nb, kNmfThreads, 0, s>>>(M, Num, G, chs, feps);
+            else if (k == 16) nmf_update_warp_kernel<16><<<nb, kNmfThreads, 0, s>>>(M, Num, G, chs, feps);
+            else if (k == 32) nmf_update_warp_kernel<32><<<nb, kNmfThreads, 0, s>>>(M, Num, G, chs, feps);
+            else nmf_update_warp_kernel<64><<<nb, kNmfThreads, 0, s>>>(M, Num, G, chs, feps);
+        };
         auto record_objective = [&](int t) {
-            nmf_cross_kernel<<<nbW, kNmfThreads, 0, s>>>(W, AH, k, dchW, cross);
+            if (blocked) nmf_cross_flat_kernel<<<nbW, kNmfThreads, 0, s>>>(W, AH, k, dchW, cross);
+            else nmf_cross_kernel<<<nbW, kNmfThreads, 0, s>>>(W, AH, k, dchW, cross);
             nmf_objective_kernel<<<ng, kNmfThreads, 0, s>>>(cross, dgW, GW, GH, da2, k, dobj + t, ostride);
         };
         // initial objective (outside the graph; also warms the SpMM launch set-up)
@@ -274,11 +451,11 @@ static int nmf_impl(spmm_mat_t A, int32_t k, int32_t steps, float* W, float* Ht,
             for (int32_t t = 0; t < steps && rc == SPMM_OK; ++t) {
                 // H step: Ht <- Ht o (A^T W) / (Ht (W^T W) + eps); GW holds W^T W
                 if ((rc = spmm(1, W, nr, AtW)) != SPMM_OK) break;
-                nmf_update_kernel<<<nbH, kNmfThreads, 0, s>>>(Ht, AtW, GW, k, dchH, feps);
+                update(Ht, AtW, GW, false);
                 gram(Ht, false, GH);
                 // W step: W <- W o (A Ht) / (W (Ht^T Ht) + eps)
                 if ((rc = spmm(0, Ht, nc, AH)) != SPMM_OK) break;
-                nmf_update_kernel<<<nbW, kNmfThreads, 0, s>>>(W, AH, GH, k, dchW, feps);
+                update(W, AH, GH, true);
                 gram(W, true, GW);
                 record_objective(t + 1);
             }

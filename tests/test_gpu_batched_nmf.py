@@ -111,3 +111,36 @@ def test_nmf_argument_errors(sp):
     with pytest.raises(sp.SpmmError):
         h.nmf(4, 3, W, H)
     h.close()
+
+
+@pytest.mark.parametrize("k", [3, 5, 16, 32, 64])
+def test_nmf_ranks_and_both_kernel_paths(sp, k):
+    """Ranks on the plain kernels (3, 5) and on the blocked Gram / warp-level
+    update / flat cross-term kernels (16, 32, 64), against the FP64 oracle;
+    at k = 16 the same factors placed off a 16-byte boundary take the plain
+    kernels, and both paths give the same objective within FP32 rounding."""
+    import torch
+    A = synth.chunglu_csr(2, seed=7, nmin=3000, nmax=3500)
+    steps = 12
+    W0, H0 = _init(A.n_rows, k, 5), _init(A.n_cols, k, 6)
+    h = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, transpose=True)
+    try:
+        W, Ht = torch.from_numpy(W0.copy()).cuda(), torch.from_numpy(H0.copy()).cuda()
+        obj = h.nmf(k, steps, W, Ht)[0]
+        Wr, Hr, objr = oracle.nmf(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, W0, H0, steps)
+        np.testing.assert_allclose(obj, objr, rtol=1e-4)
+        np.testing.assert_allclose(W.cpu().numpy(), Wr, rtol=1e-2, atol=1e-4 * np.abs(Wr).max())
+        np.testing.assert_allclose(Ht.cpu().numpy(), Hr, rtol=1e-2, atol=1e-4 * np.abs(Hr).max())
+        assert np.all(np.diff(obj) <= 1e-6 * obj[:-1])
+        if k == 16:
+            bw = torch.empty(W0.size + 1, device="cuda")
+            bh = torch.empty(H0.size + 1, device="cuda")
+            Wu = bw[1:].view(A.n_rows, k)                 # 4 bytes past a 16-byte boundary
+            Hu = bh[1:].view(A.n_cols, k)
+            Wu.copy_(torch.from_numpy(W0))
+            Hu.copy_(torch.from_numpy(H0))
+            obj_u = h.nmf(k, steps, Wu, Hu)[0]
+            np.testing.assert_allclose(obj_u, obj, rtol=1e-6)
+            np.testing.assert_allclose(Wu.cpu().numpy(), W.cpu().numpy(), rtol=1e-4, atol=1e-6 * float(W.abs().max()))
+    finally:
+        h.close()

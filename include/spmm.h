@@ -196,16 +196,17 @@ typedef struct {
  * lines and each warp task gathers from a narrower band of X (R-MAT scale 24:
  * 8-33% faster from k = 2 on, with the vectors in the new order).  Graphs
  * whose locality comes from clusters of similar degree rather than from hubs
- * lose it (a clustered block model ran 0.5-0.8x as fast at k = 8), so the flag
- * suits skewed degree distributions.  Vectors in
- * the new order ("the handle's order") go to spmm_apply_relabelled at no
- * extra cost; spmm_apply keeps the input order by gathering X's rows into the
- * handle's order and Y's rows back (two buffers the handle keeps and grows,
- * n * k elements each; spmm_apply calls on one such handle share them and
- * must not overlap, as with SPMM_REORDER's buffer).  spmm_pagerank, spmm_eigs, spmm_eigs_filtered,
- * spmm_svds and spmm_nmf take and return vectors in the input order and run
- * in the handle's order in between.  The new summation order within a row
- * gives other float32 roundings than a handle without the flag.  Not with
+ * lose it (a clustered block model ran 0.5-0.8x as fast at k = 8), so the
+ * flag suits skewed degree distributions.
+ *   Vectors in the new order ("the handle's order") go to
+ * spmm_apply_relabelled at no extra cost.  spmm_apply keeps the input order
+ * by gathering X's rows into the handle's order and Y's rows back (two
+ * buffers the handle keeps and grows, n * k elements each; spmm_apply calls
+ * on one such handle share them and must not overlap, as with SPMM_REORDER's
+ * buffer).  spmm_pagerank, spmm_eigs, spmm_eigs_filtered, spmm_svds and
+ * spmm_nmf take and return vectors in the input order and run in the
+ * handle's order in between.  The new summation order within a row gives
+ * other float32 roundings than a handle without the flag.  Not with
  * spmm_create_batched, spmm_apply_batched or the host-buffer calls
  * (spmm_apply_host, spmm_apply_host_parts: SPMM_ERR_UNSUPPORTED).
  *

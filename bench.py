@@ -1157,19 +1157,47 @@ def main():
     # step hands the sweep's X matrices (pinned host memory, one contiguous
     # row-major part per k) to spmm_apply_host_parts, which copies each part
     # in, multiplies and copies the result out on three streams so the parts
-    # overlap, and returns with every Y on the host; then PageRank runs on the
-    # device and its ranks are read back to pinned host memory.
+    # overlap, and returns with every Y on the host; PageRank runs on the
+    # device and its ranks are read back to pinned host memory.  The sweep's
+    # A X products and PageRank's A^T products use separate scratch of the
+    # handle, so PageRank runs from a second host thread while the sweep's
+    # copies hold the link (both calls block their thread; ctypes releases
+    # the GIL).  A transposed sweep, or a handle with relabelled columns,
+    # shares scratch with PageRank, so there PageRank runs after the sweep.
     e2e = None
     if not args.no_e2e:
         Xp = [X[k].cpu().pin_memory() for k in ks]
         Yp = [torch.empty((N, k), dtype=torch.float32).pin_memory() for k in ks]
         xp_host = torch.empty(N, dtype=torch.float32).pin_memory()
+        pr_stream = torch.cuda.Stream()
+        pr_err = []
+
+        def pr_part():
+            try:
+                with torch.cuda.stream(pr_stream):
+                    h.pagerank(0.85, args.pagerank_iters, x=xpr, stream=pr_stream)
+                    xp_host.copy_(xpr, non_blocking=True)
+                pr_stream.synchronize()
+            except Exception as ex:            # re-raised by the step
+                pr_err.append(ex)
+
+        overlap = bool(args.pagerank_iters) and not args.transpose and not args.reorder
 
         def e2e_step():
-            h.apply_host_parts(Xp, Yp, transpose=args.transpose, stream=stream)
-            if args.pagerank_iters:
-                h.pagerank(0.85, args.pagerank_iters, x=xpr, stream=stream)
-                xp_host.copy_(xpr, non_blocking=True)
+            t = threading.Thread(target=pr_part) if overlap else None
+            if t is not None:
+                t.start()
+            try:
+                h.apply_host_parts(Xp, Yp, transpose=args.transpose, stream=stream)
+            finally:
+                if t is not None:
+                    t.join()
+            if pr_err:
+                raise pr_err[0]
+            if args.pagerank_iters and not overlap:
+                pr_part()
+                if pr_err:
+                    raise pr_err[0]
         for _ in range(2):
             e2e_step()
         torch.cuda.synchronize()
@@ -1189,7 +1217,8 @@ def main():
         db = hb + (N * 4 if args.pagerank_iters else 0)
         e2e = {"value": world * nnz * (len(ks) + args.pagerank_iters) * reps / te, "unit": UNIT,
                "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db, "ms_per_step": 1e3 * te / reps,
-               "api": "spmm_apply_host_parts (host X and Y, one part per k) + spmm_pagerank + rank read-back",
+               "api": "spmm_apply_host_parts (host X and Y, one part per k) + spmm_pagerank + rank read-back"
+                      + (" (PageRank on a second host thread during the sweep)" if overlap else ""),
                "results_match_device": bool(ok)}
         del Xp, Yp
 

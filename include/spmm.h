@@ -17,6 +17,21 @@
  *     as void*, NULL = the legacy default stream).  spmm_apply on a resident
  *     handle does not synchronise the host and allocates nothing (the two
  *     exceptions are stated at spmm_apply).
+ *   - Concurrency: calls on one handle must not overlap (from several host
+ *     threads, or on several streams at once), with one exception.  On a
+ *     resident handle made by spmm_create_csr without SPMM_REORDER and
+ *     SPMM_RELABEL, a call that runs only A X products (spmm_apply,
+ *     spmm_apply_host or spmm_apply_host_parts with transpose = 0) may
+ *     overlap one that runs only A^T products (spmm_apply with transpose != 0,
+ *     or spmm_pagerank): each orientation has its own task counter, scratch
+ *     and hot-row buffer.  The host-buffer calls share the handle's group
+ *     buffers, so two of them never overlap.  A host-buffer call that grows
+ *     those buffers (the first, or one with wider groups) and a spmm_pagerank
+ *     call that captures its graph (the first, or one with a new x, damping
+ *     or iters) allocate, so they should not overlap anything on the handle.
+ *     The device status word is per handle: a staging timeout in either call
+ *     is reported by the first read of it (spmm_pagerank's own, or
+ *     spmm_sync_status).  Separate handles never share state.
  *   - Memory: X and Y are caller-owned DEVICE pointers; Y is overwritten, not
  *     accumulated into; X and Y must not overlap.  Handles own device copies of
  *     A made at create time.
@@ -467,7 +482,8 @@ int spmm_vpart_cols(int64_t n_in, int64_t n_out, int32_t p, spmm_dtype xtype, in
  *   stream       the multiply runs on it, after the work already queued there
  * The device buffers, two copy streams and their events are kept by the
  * handle for later calls (freed by spmm_destroy); calls on one handle must not
- * overlap.  Returns when Y is complete on the host.  The result equals
+ * overlap, except as stated under Concurrency above.  Returns when Y is
+ * complete on the host.  The result equals
  * spmm_apply on the same columns.
  * Errors: SPMM_ERR_ARG, SPMM_ERR_UNSUPPORTED (value/X type mix),
  * SPMM_ERR_OOM (the budget holds no column), SPMM_ERR_CUDA.
@@ -608,7 +624,8 @@ int spmm_static_status(void* stream);
  * 2..iters as a CUDA graph; the handle keeps them until spmm_destroy, and a
  * later call with the same x, damping and iters only launches the graph
  * (another x, damping or iters is captured anew).  Calls on one handle must
- * not overlap.  Errors: SPMM_ERR_ARG (NULL, non-square, values present, no
+ * not overlap, except with A X products as stated under Concurrency above.
+ * Errors: SPMM_ERR_ARG (NULL, non-square, values present, no
  * transpose, bad d or iters), SPMM_ERR_TIMEOUT, SPMM_ERR_OOM, SPMM_ERR_CUDA.
  */
 int spmm_pagerank(spmm_mat_t A, double damping, int32_t iters, float* x, const float* x0, double* residuals,

@@ -46,3 +46,58 @@ def test_concurrent_handles_match_serial():
         assert torch.equal(handles[i].apply(Y, transpose=True).cpu(), out[i][1])
         handles[i].sync_status()
         handles[i].close()
+
+
+def test_orientations_of_one_handle_overlap():
+    """On one handle, A X products (a host-buffer sweep and device applies)
+    from one thread and PageRank's A^T products from another run at once and
+    give the results of the same calls made one at a time."""
+    import torch
+    from paper_1602_02864_gb300 import spmm
+    A = synth.rmat_csr(15, seed=11)
+    h = spmm.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, transpose=True)
+    ks = (1, 8, 33)
+    Xp = [torch.from_numpy(synth.dense(A.n_cols, k, seed=k)).pin_memory() for k in ks]
+    Yp = [torch.empty((A.n_rows, k), dtype=torch.float32).pin_memory() for k in ks]
+    Xd = torch.from_numpy(synth.dense(A.n_cols, 4, seed=4)).cuda()
+    x = torch.empty(A.n_rows, dtype=torch.float32, device="cuda")
+    try:
+        # one at a time: these calls also grow the host-call buffers and
+        # capture the PageRank graph, which must not overlap anything
+        h.apply_host_parts(Xp, Yp)
+        Y_ref = [y.clone() for y in Yp]
+        Yd_ref = h.apply(Xd).cpu()
+        _, res_ref = h.pagerank(0.85, 12, x=x)
+        x_ref = x.cpu()
+        torch.cuda.synchronize()
+        errors = []
+
+        def ranks():
+            try:
+                s = torch.cuda.Stream()
+                for _ in range(4):
+                    _, res = h.pagerank(0.85, 12, x=x, stream=s)
+                    assert np.array_equal(res, res_ref)
+                s.synchronize()
+            except Exception as e:                 # reported below
+                errors.append(e)
+
+        for _ in range(3):
+            for y in Yp:
+                y.fill_(float("nan"))
+            t = threading.Thread(target=ranks)
+            t.start()
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                h.apply_host_parts(Xp, Yp, stream=s)
+                Yd = h.apply(Xd, stream=s)
+            s.synchronize()
+            t.join()
+            assert not errors, errors
+            for y, r in zip(Yp, Y_ref):
+                assert torch.equal(y, r)
+            assert torch.equal(Yd.cpu(), Yd_ref)
+            assert torch.equal(x.cpu(), x_ref)
+        h.sync_status()
+    finally:
+        h.close()

@@ -88,6 +88,7 @@ static int build_orientation(DevCSR& d, int64_t n_rows, int64_t n_cols, const in
     d.nnz = row_ptr[n_rows];
     HostPlan plan = build_plan(row_ptr, n_rows, p);
     std::copy(plan.walk_eff, plan.walk_eff + 4, d.walk_eff);
+    d.row_blocks = cut_row_blocks(plan, kRowBlocks);
     cudaError_t e;
     if ((e = upload(&d.row_ptr, row_ptr, (size_t)n_rows + 1, 2, s, bytes)) != cudaSuccess)
         return cuda_fail(e, "row_ptr");
@@ -709,12 +710,12 @@ cudaError_t launch_rows(const FwdArgs& a, int32_t xtype, int vmode, int vec, int
 
 // Enqueue Y = A X (or A^T X) for a validated handle; shared by spmm_apply and
 // the applications built on it.
-int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
-              int64_t ldy, cudaStream_t s) {
-    NvtxRange range(transpose ? "spmm_apply A^T X" : "spmm_apply A X");
-    if (A->streaming && !transpose) return stream_apply(A, X, ldx, k, xtype, Y, ldy, s);
+// The product over task runs: one run over all tasks (runs == nullptr), or
+// each of d.row_blocks followed by rows_done on its rows.
+static int apply_resident(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype,
+                          float* Y, int64_t ldy, cudaStream_t s,
+                          const std::function<int(int64_t, int64_t)>* rows_done) {
     const DevCSR& d = transpose ? A->tr : A->fwd;
-    if (d.n_rows == 0) return SPMM_OK;
     const int vmode = value_mode(A, xtype);
     if (vmode < 0) {
         set_error("spmm_apply: 16-bit values need X of the same 16-bit type (or use F32 values)");
@@ -741,13 +742,8 @@ int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int3
         a.Xh = d.xh;
         a.hot_bytes = (d.n_hot * k * esize + 15) & ~(int64_t)15;
     }
-    cudaError_t ec = cudaSuccess;
-    a.task_ctr = task_counter(d, k, xtype, s, &ec, &a.task_chunk);
-    if (ec != cudaSuccess) return cuda_fail(ec, "spmm_apply: task counter");
     a.row_ptr = d.row_ptr;
     a.val = d.val;
-    a.tasks = d.tasks;
-    a.n_tasks = d.n_tasks;
     a.partials = d.partials;
     a.n_slots = d.n_slots;
     a.status = A->status;
@@ -755,11 +751,46 @@ int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int3
     a.x_evict_last = A->params.x_evict_last;
     a.compensated = d.partials_comp != nullptr || (A->params.compensated && d.n_slots == 0);
     a.partials_comp = d.partials_comp;
-    cudaError_t e = launch_rows(a, xtype, vmode, vec, ch, s);
-    if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: task kernel");
-    e = launch_combine(d.splits, d.n_splits, d.partials, Y, ldy, k, s, d.partials_comp);
-    if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: combine kernel");
+    const RowBlock all{0, d.n_tasks, 0, d.n_rows, 0, d.n_splits};
+    const bool by_runs = rows_done && d.row_blocks.size() > 1;
+    const size_t n_runs = by_runs ? d.row_blocks.size() : 1;
+    for (size_t j = 0; j < n_runs; ++j) {
+        const RowBlock& b = by_runs ? d.row_blocks[j] : all;
+        cudaError_t ec = cudaSuccess;
+        a.task_ctr = task_counter(d, k, xtype, s, &ec, &a.task_chunk);
+        if (ec != cudaSuccess) return cuda_fail(ec, "spmm_apply: task counter");
+        a.tasks = d.tasks + b.t0;
+        a.n_tasks = b.t1 - b.t0;
+        cudaError_t e = launch_rows(a, xtype, vmode, vec, ch, s);
+        if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: task kernel");
+        e = launch_combine(d.splits + b.s0, b.s1 - b.s0, d.partials, Y, ldy, k, s, d.partials_comp);
+        if (e != cudaSuccess) return cuda_fail(e, "spmm_apply: combine kernel");
+        if (rows_done) {
+            const int rc = (*rows_done)(b.r0, b.r1);
+            if (rc != SPMM_OK) return rc;
+        }
+    }
     return SPMM_OK;
+}
+
+int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
+              int64_t ldy, cudaStream_t s) {
+    NvtxRange range(transpose ? "spmm_apply A^T X" : "spmm_apply A X");
+    if (A->streaming && !transpose) return stream_apply(A, X, ldx, k, xtype, Y, ldy, s);
+    if ((transpose ? A->tr : A->fwd).n_rows == 0) return SPMM_OK;
+    return apply_resident(A, transpose, X, ldx, k, xtype, Y, ldy, s, nullptr);
+}
+
+int apply_dev_runs(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
+                   int64_t ldy, cudaStream_t s, const std::function<int(int64_t, int64_t)>& rows_done) {
+    NvtxRange range(transpose ? "spmm_apply A^T X (runs)" : "spmm_apply A X (runs)");
+    const DevCSR& d = transpose ? A->tr : A->fwd;
+    if (d.n_rows == 0) return SPMM_OK;
+    if (A->streaming && !transpose) {
+        const int rc = stream_apply(A, X, ldx, k, xtype, Y, ldy, s);
+        return rc != SPMM_OK ? rc : rows_done(0, d.n_rows);
+    }
+    return apply_resident(A, transpose, X, ldx, k, xtype, Y, ldy, s, &rows_done);
 }
 
 }  // namespace spmm
@@ -939,6 +970,7 @@ static int replan_orientation(DevCSR& d, const Params& p, cudaStream_t s, int64_
     d.partials = partials;
     d.n_slots = plan.n_slots;
     std::copy(plan.walk_eff, plan.walk_eff + 4, d.walk_eff);
+    d.row_blocks = cut_row_blocks(plan, kRowBlocks);
     d.short_runs = p.short_runs;
     return SPMM_OK;
 }

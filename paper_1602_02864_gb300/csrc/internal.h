@@ -5,6 +5,7 @@
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -57,6 +58,15 @@ struct HostPlan {
     double walk_eff[4] = {1.0, 1.0, 1.0, 1.0};
 };
 
+// A run of whole warp tasks t0 .. t1-1 covering rows r0 .. r1-1 (the
+// segments of a split row are never in two runs), whose split rows are
+// splits s0 .. s1-1.  The host-buffer calls multiply run by run and copy a
+// run's rows of Y out while the next run multiplies.
+struct RowBlock {
+    int64_t t0, t1, r0, r1, s0, s1;
+};
+constexpr int kRowBlocks = 4;
+
 // Device-side copy of one orientation (CSR of A, or CSR of A^T == CSC of A).
 struct DevCSR {
     int64_t n_rows = 0, n_cols = 0, nnz = 0;
@@ -84,6 +94,7 @@ struct DevCSR {
     int64_t n_hot = 0;
     void* xh = nullptr;
     double walk_eff[4] = {1.0, 1.0, 1.0, 1.0};   // HostPlan::walk_eff of the current plan
+    std::vector<RowBlock> row_blocks;             // kRowBlocks runs of the current plan
 };
 
 // Streaming mode: the matrix stays in (pinned) host memory and flows to HBM
@@ -203,6 +214,8 @@ namespace spmm {
 
 // plan.cpp
 HostPlan build_plan(const int64_t* row_ptr, int64_t n_rows, const Params& p);
+// at most nb runs of the plan's tasks with about equal stored entries
+std::vector<RowBlock> cut_row_blocks(const HostPlan& plan, int nb);
 
 // vpart.cu
 void hostio_release(spmm_mat* A);
@@ -274,6 +287,11 @@ void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
               int64_t ldy, cudaStream_t s);
+// apply_dev run by run (RowBlock): after a run's task kernel and the combine
+// pass of its split rows, rows_done(r0, r1) enqueues what needs those rows of
+// Y.  One run over all rows for streaming handles and plans without runs.
+int apply_dev_runs(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
+                   int64_t ldy, cudaStream_t s, const std::function<int(int64_t, int64_t)>& rows_done);
 // the task counter for a launch over rows of k elements of xtype (reset on s;
 // nullptr for the static schedule) and the number of tasks per claim
 unsigned long long* task_counter(const DevCSR& d, int32_t k, int32_t xtype, cudaStream_t s, cudaError_t* e,

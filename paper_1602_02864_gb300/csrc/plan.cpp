@@ -91,4 +91,36 @@ HostPlan build_plan(const int64_t* row_ptr, int64_t n_rows, const Params& p) {
     return plan;
 }
 
+// Run j ends at the first task that starts at or after (j + 1) / nb of the
+// stored entries and begins a new row (consecutive tasks share a first row
+// only as segments of one split row).  The sentinel's row is n_rows.
+std::vector<RowBlock> cut_row_blocks(const HostPlan& plan, int nb) {
+    std::vector<RowBlock> out;
+    const size_t nt = plan.tasks.size() - 1;
+    if (nt == 0 || nb < 1) return out;
+    auto e0 = [&](size_t t) { return ((int64_t)(uint32_t)plan.tasks[t].z) | ((int64_t)plan.tasks[t].w << 32); };
+    auto row = [&](size_t t) { return (int64_t)plan.tasks[t].x; };
+    const int64_t total = e0(nt);
+    size_t t = 0, sp = 0;
+    for (int j = 0; j < nb && t < nt; ++j) {
+        RowBlock b;
+        b.t0 = (int64_t)t;
+        b.r0 = row(t);
+        b.s0 = (int64_t)sp;
+        size_t u = nt;
+        if (j < nb - 1) {
+            const int64_t goal = total / nb * (j + 1) + total % nb * (j + 1) / nb;
+            u = t + 1;
+            while (u < nt && (e0(u) < goal || row(u) == row(u - 1))) ++u;
+        }
+        b.t1 = (int64_t)u;
+        b.r1 = row(u);
+        while (sp < plan.splits.size() && (int64_t)plan.splits[sp].x < b.r1) ++sp;
+        b.s1 = (int64_t)sp;
+        out.push_back(b);
+        t = u;
+    }
+    return out;
+}
+
 }  // namespace spmm

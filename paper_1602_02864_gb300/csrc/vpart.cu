@@ -181,21 +181,30 @@ int run_groups(spmm_mat* A, const std::vector<Group>& groups, int32_t xtype, int
                                        cudaMemcpyHostToDevice, h.s_in)) != cudaSuccess)
             break;
         if ((e = cudaEventRecord(x_ready[b], h.s_in)) != cudaSuccess) break;
-        // multiply (Y buffer b is free once group i-2 has been copied out)
+        // multiply (Y buffer b is free once group i-2 has been copied out),
+        // run by run: each run's rows of Y leave while the next run multiplies
         if ((e = cudaStreamWaitEvent(s, x_ready[b], 0)) != cudaSuccess) break;
         if (i >= 2 && (e = cudaStreamWaitEvent(s, y_free[b], 0)) != cudaSuccess) break;
+        // copy-out of rows r0 .. r1-1 of group i (the wait takes the event's
+        // latest record, so one event serves every run)
+        auto rows_out = [&](int64_t r0, int64_t r1) -> int {
+            cudaError_t ce = cudaEventRecord(y_ready[b], s);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h.s_out, y_ready[b], 0);
+            if (ce == cudaSuccess && r1 > r0)
+                ce = copy_rows(reinterpret_cast<char*>(gr.y) + (size_t)r0 * gr.y_pitch, gr.y_pitch,
+                               h.y[b] + (size_t)r0 * w, (size_t)(w * 4), (size_t)(w * 4), (size_t)(r1 - r0),
+                               cudaMemcpyDeviceToHost, h.s_out);
+            return ce == cudaSuccess ? SPMM_OK : cuda_fail(ce, "spmm_apply_host: copy-out");
+        };
         if (n_in > 0) {
-            if ((rc = apply_dev(A, transpose, h.x[b], w, w, xtype, h.y[b], w, s)) != SPMM_OK) return rc;
-        } else if ((e = cudaMemsetAsync(h.y[b], 0, (size_t)(n_out * w * 4), s)) != cudaSuccess) {
+            if ((rc = apply_dev_runs(A, transpose, h.x[b], w, w, xtype, h.y[b], w, s, rows_out)) != SPMM_OK)
+                return rc;
+        } else if ((e = cudaMemsetAsync(h.y[b], 0, (size_t)(n_out * w * 4), s)) != cudaSuccess ||
+                   (rc = rows_out(0, n_out)) != SPMM_OK) {
+            if (rc != SPMM_OK) return rc;
             break;
         }
         if ((e = cudaEventRecord(x_free[b], s)) != cudaSuccess) break;
-        if ((e = cudaEventRecord(y_ready[b], s)) != cudaSuccess) break;
-        // copy-out of group i
-        if ((e = cudaStreamWaitEvent(h.s_out, y_ready[b], 0)) != cudaSuccess) break;
-        if ((e = copy_rows(gr.y, gr.y_pitch, h.y[b], (size_t)(w * 4), (size_t)(w * 4), (size_t)n_out,
-                           cudaMemcpyDeviceToHost, h.s_out)) != cudaSuccess)
-            break;
         if ((e = cudaEventRecord(y_free[b], h.s_out)) != cudaSuccess) break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "spmm_apply_host: group pipeline");

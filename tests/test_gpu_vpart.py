@@ -155,3 +155,49 @@ def test_parts_errors(sp, rmat14, handles):
         hp.apply_host_parts([X], [Y])                      # a part wider than 64 columns
     with pytest.raises(ValueError):
         hp.apply_host_parts([X[:, :4].copy()], [])         # unequal part lists
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_parts_by_runs_with_split_rows(sp, transpose):
+    """The host-buffer calls multiply in runs of whole tasks and copy each
+    run's rows out while the next run multiplies: with many split hub rows
+    (short tasks, low split threshold) and hot columns at k = 1, every part
+    equals the device product bit for bit and the oracle exactly."""
+    import torch
+    A = synth.rmat_csr(13, seed=21)
+    o = sp.spmm_opts(task_nnz=32, long_row=64, short_max=15, hot_cols=512)
+    h = sp.SparseMatrix(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, transpose=True, opts=o)
+    try:
+        info = h.info()
+        assert info["n_split_rows"] > 50 and info["n_hot"] > 0
+        widths = [1, 8, 33]
+        X = synth.dense(A.n_rows, sum(widths), seed=6, mode="int")
+        cuts = np.cumsum([0] + widths)
+        Xp = [np.ascontiguousarray(X[:, a:b]) for a, b in zip(cuts[:-1], cuts[1:])]
+        Yp = [np.full((A.n_rows, w), np.nan, dtype=np.float32) for w in widths]
+        h.apply_host_parts(Xp, Yp, transpose=transpose)
+        for x, y in zip(Xp, Yp):
+            assert torch.equal(h.apply(to_dev(x), transpose=transpose).cpu(), torch.from_numpy(y))
+        ref = oracle.spmm(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, None, X, transpose=transpose)
+        assert np.array_equal(np.concatenate(Yp, axis=1).astype(np.float64), ref)
+        h.sync_status()
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("n,edges", [(3, [(0, 1), (2, 0)]), (40, []), (1, [(0, 0)])])
+def test_parts_tiny_and_empty(sp, n, edges):
+    """Fewer tasks than runs, and no stored entries at all."""
+    rp = np.zeros(n + 1, dtype=np.int64)
+    for r, _ in edges:
+        rp[r + 1:] += 1
+    ci = np.array([c for _, c in sorted(edges)], dtype=np.int32)
+    h = sp.SparseMatrix(n, n, rp, ci, None, transpose=True)
+    try:
+        X = synth.dense(n, 5, seed=1, mode="int")
+        Y = np.full((n, 5), np.nan, dtype=np.float32)
+        h.apply_host_parts([X], [Y])
+        ref = oracle.spmm(n, n, rp, ci, None, X)
+        assert np.array_equal(Y.astype(np.float64), ref)
+    finally:
+        h.close()

@@ -708,10 +708,8 @@ cudaError_t launch_rows(const FwdArgs& a, int32_t xtype, int vmode, int vec, int
     return launch_rows_f16(a, vmode, vec, ch, s);
 }
 
-// Enqueue Y = A X (or A^T X) for a validated handle; shared by spmm_apply and
-// the applications built on it.
-// The product over task runs: one run over all tasks (runs == nullptr), or
-// each of d.row_blocks followed by rows_done on its rows.
+// The product on a resident handle: one run over all tasks (rows_done ==
+// nullptr), or each of d.row_blocks followed by rows_done on its rows.
 static int apply_resident(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype,
                           float* Y, int64_t ldy, cudaStream_t s,
                           const std::function<int(int64_t, int64_t)>* rows_done) {
@@ -773,6 +771,8 @@ static int apply_resident(const spmm_mat* A, int transpose, const void* X, int64
     return SPMM_OK;
 }
 
+// Enqueue Y = A X (or A^T X) for a validated handle; shared by spmm_apply and
+// the applications built on it.
 int apply_dev(const spmm_mat* A, int transpose, const void* X, int64_t ldx, int32_t k, int32_t xtype, float* Y,
               int64_t ldy, cudaStream_t s) {
     NvtxRange range(transpose ? "spmm_apply A^T X" : "spmm_apply A X");

@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-part-cols", type=int, default=16,
+                    help="end-to-end step: X_k and Y_k live in host memory as vertical partitions of at most "
+                         "this many columns (Section 3.3), one pass over A each")
     ap.add_argument("--no-ceiling", "--no-gather-probe", dest="no_ceiling", action="store_true",
                     help="skip the gather probes (reference rates of X-row gathers alone)")
     ap.add_argument("--no-stream", action="store_true",
@@ -1154,10 +1157,13 @@ def main():
         parity[str(k)] = float((np.abs(got - ref) / np.maximum(scale[k], 1e-300)).max())
 
     # ---- end to end through the library's host-buffer entry point: every
-    # step hands the sweep's X matrices (pinned host memory, one contiguous
-    # row-major part per k) to spmm_apply_host_parts, which copies each part
-    # in, multiplies and copies the result out on three streams so the parts
-    # overlap, and returns with every Y on the host; PageRank runs on the
+    # step hands the sweep's X matrices to spmm_apply_host_parts, each X_k in
+    # pinned host memory as vertical partitions of at most P columns, each
+    # partition a contiguous row-major array (the paper's layout for dense
+    # matrices outside memory, Section 3.3; a k wider than P takes one pass
+    # over A per partition).  The call copies each part in, multiplies and
+    # copies the result out on three streams so the parts overlap, and
+    # returns with every Y partition on the host; PageRank runs on the
     # device and its ranks are read back to pinned host memory.  The sweep's
     # A X products and PageRank's A^T products use separate scratch of the
     # handle, so PageRank runs from a second host thread while the sweep's
@@ -1166,8 +1172,10 @@ def main():
     # shares scratch with PageRank, so there PageRank runs after the sweep.
     e2e = None
     if not args.no_e2e:
-        Xp = [X[k].cpu().pin_memory() for k in ks]
-        Yp = [torch.empty((N, k), dtype=torch.float32).pin_memory() for k in ks]
+        P = max(1, min(64, args.e2e_part_cols))
+        cuts = [(k, c0, min(k, c0 + P)) for k in ks for c0 in range(0, k, P)]
+        Xp = [X[k][:, c0:c1].contiguous().cpu().pin_memory() for k, c0, c1 in cuts]
+        Yp = [torch.empty((N, c1 - c0), dtype=torch.float32).pin_memory() for _, c0, c1 in cuts]
         xp_host = torch.empty(N, dtype=torch.float32).pin_memory()
         pr_stream = torch.cuda.Stream()
         pr_err = []
@@ -1198,6 +1206,9 @@ def main():
                 pr_part()
                 if pr_err:
                     raise pr_err[0]
+        # one call alone first: it grows the handle's group buffers, which
+        # must not overlap other calls on the handle
+        h.apply_host_parts(Xp, Yp, transpose=args.transpose, stream=stream)
         for _ in range(2):
             e2e_step()
         torch.cuda.synchronize()
@@ -1210,15 +1221,21 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         te = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0)
-        ok = all(torch.equal(Yp[i], Y[k].cpu()) for i, k in enumerate(ks))
+        # each Y partition against a device product of the same columns (the
+        # sweep's own result where the partition is the whole X_k)
+        ok = all(torch.equal(Yp[i], (Y[k] if c1 - c0 == k else
+                                     h.apply(X[k][:, c0:c1].contiguous(), transpose=args.transpose)).cpu())
+                 for i, (k, c0, c1) in enumerate(cuts))
         if args.pagerank_iters:
             ok = ok and torch.equal(xp_host, xpr.cpu())
         hb = sum(N * k * 4 for k in ks)
         db = hb + (N * 4 if args.pagerank_iters else 0)
         e2e = {"value": world * nnz * (len(ks) + args.pagerank_iters) * reps / te, "unit": UNIT,
                "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db, "ms_per_step": 1e3 * te / reps,
-               "api": "spmm_apply_host_parts (host X and Y, one part per k) + spmm_pagerank + rank read-back"
+               "api": "spmm_apply_host_parts (host X and Y, each X_k and Y_k as vertical partitions of at "
+                      f"most {P} columns: {len(cuts)} parts, one pass over A each) + spmm_pagerank + rank read-back"
                       + (" (PageRank on a second host thread during the sweep)" if overlap else ""),
+               "part_cols": P, "passes_over_A": len(cuts),
                "results_match_device": bool(ok)}
         del Xp, Yp
 

@@ -465,9 +465,11 @@ int spmm_vpart_cols(int64_t n_in, int64_t n_out, int32_t p, spmm_dtype xtype, in
  * vertical partitions (Section 3.3; the paper's external medium is SSD, here
  * it is host memory).  The p columns are processed in groups of g columns,
  * one pass over A per group: a 2-D copy of the group's columns to the device,
- * the SpMM, a 2-D copy of the group's result back into Y's columns.  Copy-in,
- * multiply and copy-out run on three streams with two device buffers for X
- * and for Y, so consecutive groups overlap.
+ * the SpMM in four runs of whole row tasks, and after each run a 2-D copy of
+ * its rows of the result back into Y's columns.  Copy-in, multiply and
+ * copy-out run on three streams with two device buffers for X and for Y, so
+ * consecutive groups overlap, and a group's first rows leave while its last
+ * rows multiply.
  *   A            handle (resident or streaming)
  *   X            host, row-major, n_in x p with leading dimension ldx >= p
  *                elements, element type xtype (F32, BF16 or F16); pinned

@@ -9,10 +9,12 @@
 // Here the memory is HBM, the external medium is host memory, and a partition
 // is a group of g columns of X (and the same columns of Y).  Per group:
 // a 2-D copy of its columns host -> device (copy-in stream), the task kernel
-// on the caller's stream, a 2-D copy of the result device -> host (copy-out
-// stream).  X and Y have two device buffers each, so the copy-in of group
-// i+1 and the copy-out of group i-1 run while group i multiplies.  The
-// buffers, streams and events stay with the handle for later calls.
+// on the caller's stream in a few runs of whole tasks (RowBlock), and after
+// each run a 2-D copy of its rows of the result device -> host (copy-out
+// stream), so a group's result leaves while the rest of it multiplies.  X and
+// Y have two device buffers each, so the copy-in of group i+1 and the
+// copy-out of group i-1 run while group i multiplies.  The buffers, streams
+// and events stay with the handle for later calls.
 //
 // spmm_apply_host takes ordinary row-major X and Y (any leading dimension) and
 // copies each group's columns with strided 2-D copies; spmm_apply_host_parts

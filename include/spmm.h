@@ -551,6 +551,28 @@ int spmm_plan_tasks(int64_t n_rows, const int64_t* row_ptr, const spmm_opts* opt
 int spmm_plan_walk_eff(int64_t n_rows, const int64_t* row_ptr, const spmm_opts* opts, double* walk_eff);
 
 /*
+ * spmm_plan_runs -- host-only: the runs of whole tasks into which the
+ * host-buffer calls (spmm_apply_host, spmm_apply_host_parts) cut a product
+ * of the plan spmm_plan_tasks builds, so that a run's rows of Y can be copied
+ * out while the next run multiplies (they use 4 runs).  Run j ends at the
+ * first task that starts at or after (j + 1) / max_runs of the stored entries
+ * and begins a new row, so the segments of a split row stay in one run.
+ *   row_ptr   n_rows+1 int64 (host)
+ *   opts      tuning knobs or NULL
+ *   max_runs  >= 1
+ *   runs      out: room for max_runs x 6 int64 {t0, t1, r0, r1, s0, s1}: tasks
+ *             t0..t1-1, rows r0..r1-1, split rows s0..s1-1 (in the order of
+ *             the plan's split rows); consecutive runs meet, the first starts
+ *             at 0 and the last ends at the task, row and split-row counts
+ *   n_runs    out: number of runs (fewer than max_runs for small plans, 0 for
+ *             a plan without tasks)
+ * Errors: SPMM_ERR_ARG (null pointer, max_runs < 1, bad n_rows),
+ * SPMM_ERR_FORMAT (row_ptr not monotone or row_ptr[0] != 0), SPMM_ERR_OOM.
+ */
+int spmm_plan_runs(int64_t n_rows, const int64_t* row_ptr, const spmm_opts* opts, int32_t max_runs, int64_t* runs,
+                   int32_t* n_runs);
+
+/*
  * spmm_apply_csr_static -- Y = A X without allocating device memory.  The
  * paper has no counterpart; this exists for callers that cannot call
  * cudaMalloc (for example code inside a framework that hands out all device

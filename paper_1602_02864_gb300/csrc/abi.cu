@@ -233,6 +233,31 @@ extern "C" int spmm_plan_walk_eff(int64_t n_rows, const int64_t* row_ptr, const 
     return SPMM_OK;
 }
 
+extern "C" int spmm_plan_runs(int64_t n_rows, const int64_t* row_ptr, const spmm_opts* opts, int32_t max_runs,
+                              int64_t* runs, int32_t* n_runs) {
+    if (!row_ptr || !runs || !n_runs || max_runs < 1 || n_rows < 0 || n_rows >= (int64_t)1 << 31) {
+        set_error("spmm_plan_runs: bad argument");
+        return SPMM_ERR_ARG;
+    }
+    if (row_ptr[0] != 0) { set_error("spmm_plan_runs: row_ptr[0] != 0"); return SPMM_ERR_FORMAT; }
+    for (int64_t i = 0; i < n_rows; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) { set_error("spmm_plan_runs: row_ptr decreases"); return SPMM_ERR_FORMAT; }
+    try {
+        const HostPlan plan = build_plan(row_ptr, n_rows, resolve_params(opts));
+        const std::vector<RowBlock> rb = cut_row_blocks(plan, max_runs);
+        for (size_t j = 0; j < rb.size(); ++j) {
+            const RowBlock& b = rb[j];
+            const int64_t v[6] = {b.t0, b.t1, b.r0, b.r1, b.s0, b.s1};
+            std::copy(v, v + 6, runs + 6 * j);
+        }
+        *n_runs = (int32_t)rb.size();
+    } catch (const std::bad_alloc&) {
+        set_error("spmm_plan_runs: out of host memory");
+        return SPMM_ERR_OOM;
+    }
+    return SPMM_OK;
+}
+
 extern "C" const char* spmm_last_error(void) { return g_error.c_str(); }
 
 namespace spmm {

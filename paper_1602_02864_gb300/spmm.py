@@ -84,6 +84,8 @@ _lib.spmm_plan_tasks.argtypes = [_i64, _P, ctypes.POINTER(spmm_opts), _P, ctypes
 _lib.spmm_plan_tasks.restype = ctypes.c_int
 _lib.spmm_plan_walk_eff.argtypes = [_i64, _P, ctypes.POINTER(spmm_opts), ctypes.POINTER(ctypes.c_double)]
 _lib.spmm_plan_walk_eff.restype = ctypes.c_int
+_lib.spmm_plan_runs.argtypes = [_i64, _P, ctypes.POINTER(spmm_opts), _i32, _P, ctypes.POINTER(_i32)]
+_lib.spmm_plan_runs.restype = ctypes.c_int
 _lib.spmm_apply_csr_static.argtypes = [_i64, _i64, _i64, _P, _P, _P, ctypes.c_int, _P, _i64, _i64, _P, _i64,
                                        _i32, ctypes.c_int, _P, _i64, _P]
 _lib.spmm_apply_csr_static.restype = ctypes.c_int
@@ -287,6 +289,17 @@ def spmm_plan_tasks(row_ptr, opts: spmm_opts | None = None):
     _check(_lib.spmm_plan_tasks(n_rows, _ptr(rp), o, _ptr(tasks), ctypes.byref(nt), ctypes.byref(ns),
                                 ctypes.byref(nseg)))
     return tasks, ns.value, nseg.value
+
+
+def spmm_plan_runs(row_ptr, max_runs=4, opts: spmm_opts | None = None) -> np.ndarray:
+    """Host-only runs of whole tasks of the plan (the host-buffer calls use
+    4): int64 [n_runs, 6] rows {t0, t1, r0, r1, s0, s1}."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    out = np.zeros((max(int(max_runs), 1), 6), dtype=np.int64)
+    n = ctypes.c_int32(0)
+    o = ctypes.byref(opts) if opts is not None else None
+    _check(_lib.spmm_plan_runs(len(rp) - 1, _ptr(rp), o, int(max_runs), _ptr(out), ctypes.byref(n)))
+    return out[:n.value]
 
 
 def spmm_plan_walk_eff(row_ptr, opts: spmm_opts | None = None) -> list[float]:

@@ -192,3 +192,69 @@ def test_walk_eff_rejects_bad_row_ptr(sp):
         sp.spmm_plan_walk_eff(np.array([1, 2, 3], dtype=np.int64))
     with pytest.raises(sp.SpmmError):
         sp.spmm_plan_walk_eff(np.array([0, 5, 3], dtype=np.int64))
+
+
+def check_runs(sp, rp, max_runs, opts=None):
+    """The runs of whole tasks the host-buffer calls multiply one at a time:
+    they tile the task list, the rows and the split rows in order, never cut
+    between two segments of one split row, and each run but the last ends at
+    the first task boundary past its share of the stored entries."""
+    tasks, n_split, _ = sp.spmm_plan_tasks(rp, opts)
+    runs = sp.spmm_plan_runs(rp, max_runs, opts)
+    nt, n = len(tasks) - 1, len(rp) - 1
+    if nt == 0:
+        assert len(runs) == 0
+        return runs
+    e0 = (tasks[:, 2].astype(np.int64) & 0xFFFFFFFF) | (tasks[:, 3].astype(np.int64) << 32)
+    split_rows = np.array(sorted({int(t[0]) for t in tasks[:-1] if t[1] < 0}), dtype=np.int64)
+    assert split_rows.size == n_split
+    assert 1 <= len(runs) <= max_runs
+    assert runs[0, 0] == 0 and runs[0, 2] == 0 and runs[0, 4] == 0
+    assert runs[-1, 1] == nt and runs[-1, 3] == n and runs[-1, 5] == n_split
+    total = int(rp[-1])
+    for j, (t0, t1, r0, r1, s0, s1) in enumerate(runs):
+        assert t0 < t1
+        if j + 1 < len(runs):
+            assert (t1, r1, s1) == tuple(runs[j + 1, [0, 2, 4]])
+        assert r0 == tasks[t0, 0] and r1 == tasks[t1, 0]          # rows of the run's tasks
+        assert t0 == 0 or tasks[t0, 0] != tasks[t0 - 1, 0]        # a split row is never cut
+        # the split rows of the run are exactly those among its rows
+        assert list(split_rows[s0:s1]) == [r for r in split_rows if r0 <= r < r1]
+        if j + 1 < len(runs):
+            goal = total * (j + 1) // max_runs
+            assert e0[t1] >= goal
+            # no earlier boundary past the goal that starts a new row
+            for u in range(t0 + 1, t1):
+                assert e0[u] < goal or tasks[u, 0] == tasks[u - 1, 0]
+    return runs
+
+
+@pytest.mark.parametrize("max_runs", [1, 2, 4, 7])
+def test_runs_invariants_rmat(sp, max_runs):
+    A = synth.rmat_csr(12, seed=3)
+    runs = check_runs(sp, A.row_ptr, max_runs)
+    assert len(runs) == max_runs
+    o = sp.spmm_opts(task_nnz=32, long_row=64, short_max=15)    # many split rows
+    check_runs(sp, A.row_ptr, max_runs, o)
+
+
+def test_runs_small_and_special(sp):
+    assert len(check_runs(sp, np.zeros(1, dtype=np.int64), 4)) == 0          # no rows
+    assert len(check_runs(sp, np.zeros(41, dtype=np.int64), 4)) == 1         # 40 empty rows, one task
+    # one hub row split into many segments followed by short rows: the hub's
+    # segments stay together although they hold most of the entries
+    rp = np.concatenate([[0, 5000], 5000 + np.arange(1, 200)]).astype(np.int64)
+    runs = check_runs(sp, rp, 4)
+    assert runs[0, 2] == 0 and runs[0, 3] >= 1
+    for opts in (None, sp.spmm_opts(task_nnz=64, long_row=64, short_max=3)):
+        for seed in range(4):
+            rng = np.random.default_rng(seed)
+            deg = rng.zipf(1.8, size=500).clip(0, 3000)
+            check_runs(sp, np.concatenate([[0], np.cumsum(deg)]).astype(np.int64), 4, opts)
+
+
+def test_runs_reject_bad_input(sp):
+    with pytest.raises(sp.SpmmError, match="ERR_FORMAT"):
+        sp.spmm_plan_runs(np.array([0, 3, 2], dtype=np.int64))
+    with pytest.raises(sp.SpmmError, match="ERR_ARG"):
+        sp.spmm_plan_runs(np.array([0, 1], dtype=np.int64), 0)

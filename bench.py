@@ -1216,8 +1216,11 @@ def main():
         t0 = time.perf_counter()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        step_s = []                     # host time of each step (each ends with its results on the host)
         for _ in range(reps):
+            ts = time.perf_counter()
             e2e_step()
+            step_s.append(time.perf_counter() - ts)
         e1.record(stream)
         torch.cuda.synchronize()
         te = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0)
@@ -1236,6 +1239,8 @@ def main():
                       f"most {P} columns: {len(cuts)} parts, one pass over A each) + spmm_pagerank + rank read-back"
                       + (" (PageRank on a second host thread during the sweep)" if overlap else ""),
                "part_cols": P, "passes_over_A": len(cuts),
+               "step_ms": [round(1e3 * x, 2) for x in step_s],
+               "median_step_ms": round(1e3 * statistics.median(step_s), 2),
                "results_match_device": bool(ok)}
         del Xp, Yp
 

@@ -182,6 +182,13 @@ def record_traffic(csv_path, args):
     print(json.dumps(rec))
 
 
+def vertical_parts(ks, P):
+    """The end-to-end step's vertical partitions (Section 3.3): for each k in
+    order, (k, c0, c1) for columns c0..c1-1 of X_k, at most P columns each."""
+    P = max(1, min(64, int(P)))
+    return [(k, c0, min(k, c0 + P)) for k in ks for c0 in range(0, k, P)]
+
+
 def pagerank_iter_bytes(nnz, n):
     """Algorithmic bytes of one PageRank iteration: the A^T product at k = 1
     (column indices, row pointers, z in, y out) plus the update (y, x read and
@@ -1173,7 +1180,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         P = max(1, min(64, args.e2e_part_cols))
-        cuts = [(k, c0, min(k, c0 + P)) for k in ks for c0 in range(0, k, P)]
+        cuts = vertical_parts(ks, P)
         Xp = [X[k][:, c0:c1].contiguous().cpu().pin_memory() for k, c0, c1 in cuts]
         Yp = [torch.empty((N, c1 - c0), dtype=torch.float32).pin_memory() for _, c0, c1 in cuts]
         xp_host = torch.empty(N, dtype=torch.float32).pin_memory()

@@ -15,3 +15,18 @@ def test_comment_edits_keep_the_digest_code_edits_change_it():
     changed = "__global__ void k(float* y) {\n    y[0] = 2.f;\n}\n"
     assert bench.code_tokens(base) == bench.code_tokens(reworded)
     assert bench.code_tokens(base) != bench.code_tokens(changed)
+
+
+def test_vertical_parts_cover_every_column_once():
+    ks = [1, 2, 4, 8, 16, 32, 64]
+    for P in (1, 3, 16, 32, 64, 100):
+        parts = bench.vertical_parts(ks, P)
+        w = min(64, max(1, P))
+        assert all(1 <= c1 - c0 <= w for _, c0, c1 in parts)
+        for k in ks:
+            mine = [(c0, c1) for kk, c0, c1 in parts if kk == k]
+            assert mine[0][0] == 0 and mine[-1][1] == k                      # whole X_k, in order
+            assert all(a[1] == b[0] for a, b in zip(mine, mine[1:]))
+            assert len(mine) == -(-k // w)                                     # one pass over A each
+        assert sum(c1 - c0 for _, c0, c1 in parts) == sum(ks)                 # the bytes the step moves
+    assert len(bench.vertical_parts(ks, 16)) == 11

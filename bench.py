@@ -37,6 +37,7 @@ import synth  # noqa: E402
 
 UNIT = "nnz/s"
 L2_FLUSH_BYTES = 512 << 20
+NOMINAL_HBM_GBS = 8000.0     # nominal HBM3e bandwidth of the part (about 8 TB/s), reported beside the measured peak
 
 
 def parse():
@@ -1075,7 +1076,8 @@ def main():
         ms = statistics.median(per_k[k])
         B = alg_bytes(nnz, N, N, k, 4)
         breakdown[str(k)] = {"ms": round(ms, 4), "nnz_per_s": nnz / (ms / 1e3), "alg_GBps": B / (ms / 1e3) / 1e9,
-                             "roofline_frac": B / (ms / 1e3) / 1e9 / peak_gbs}
+                             "roofline_frac": B / (ms / 1e3) / 1e9 / peak_gbs,
+                             "frac_of_nominal": B / (ms / 1e3) / 1e9 / NOMINAL_HBM_GBS}
     pagerank = None
     if args.pagerank_iters:
         ms = statistics.median(pr_ms)
@@ -1382,7 +1384,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": dom["alg_GBps"], "peak": peak_gbs, "unit": "GB/s",
                          "frac": dom["roofline_frac"], "traffic": traffic, "traffic_source": traffic_src,
                          "kernel": dom_name, "peak_kind": peak_kind,
-                         "alg_bytes_per_launch": alg_bytes(nnz, N, N, kdom, 4)},
+                         "alg_bytes_per_launch": alg_bytes(nnz, N, N, kdom, 4),
+                         "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": dom["alg_GBps"] / NOMINAL_HBM_GBS},
             "pagerank": pagerank,
             "gather_probe": {"per_k": ceilings, "pagerank": pr_ceiling,
                                "note": "rows/s of gathers alone: uniform = random rows of an X-sized table "

@@ -190,6 +190,25 @@ def vertical_parts(ks, P):
     return [(k, c0, min(k, c0 + P)) for k in ks for c0 in range(0, k, P)]
 
 
+def host_cpu() -> str:
+    """The host's CPU as /proc/cpuinfo names it (model name on x86, the
+    implementer and part numbers on Arm), with its logical core count."""
+    import platform
+    name = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = {}
+            for line in f:
+                if ":" in line:
+                    key, val = (t.strip() for t in line.split(":", 1))
+                    info.setdefault(key, val)
+        name = info.get("model name") or " ".join(
+            f"{k} {info[k]}" for k in ("CPU implementer", "CPU part") if k in info)
+    except OSError:
+        pass
+    return f"{platform.machine()} {name}".strip() + f", {os.cpu_count()} logical cores"
+
+
 def pagerank_iter_bytes(nnz, n):
     """Algorithmic bytes of one PageRank iteration: the A^T product at k = 1
     (column indices, row pointers, z in, y out) plus the update (y, x read and
@@ -322,7 +341,8 @@ def reference_arm(args, rank, world):
                    "nnz": A.nnz, "ks": ks},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{len(rows)} seeded rows ({nz} nonzeros) of the scale-{args.scale} graph, "
-                                   f"all k in the sweep, plus {pr} full PageRank iteration, per step"},
+                                   f"all k in the sweep, plus {pr} full PageRank iteration, per step",
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -1312,7 +1332,8 @@ def main():
         dt = run_cpu_oracle(A, Xh, ks, rows, threads, pr)
         cpu = {"value": (nz * len(ks) + pr * nnz) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{len(rows)} seeded rows ({nz} nonzeros) of the scale-{args.scale} graph, FP64, "
-                         f"every k in the sweep, plus {pr} full PageRank iteration (serial) ({dt:.1f} s)"}
+                         f"every k in the sweep, plus {pr} full PageRank iteration (serial) ({dt:.1f} s)",
+               "host": host_cpu()}
         # the same oracle on one host thread (a smaller sample, SpMM rows only)
         rows1, nz1 = cpu_sample_rows(A, max(nz // max(threads, 1), 10_000), seed=10)
         dt1 = run_cpu_oracle(A, Xh, ks, rows1, 1)

@@ -30,3 +30,10 @@ def test_vertical_parts_cover_every_column_once():
             assert len(mine) == -(-k // w)                                     # one pass over A each
         assert sum(c1 - c0 for _, c0, c1 in parts) == sum(ks)                 # the bytes the step moves
     assert len(bench.vertical_parts(ks, 16)) == 11
+
+
+def test_host_cpu_names_the_machine_and_cores():
+    import os
+    import platform
+    s = bench.host_cpu()
+    assert s.startswith(platform.machine()) and s.endswith(f"{os.cpu_count()} logical cores")

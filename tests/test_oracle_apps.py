@@ -35,6 +35,19 @@ def test_pagerank_vs_dense_google_matrix():
     assert res.shape == (30,) and np.all(res >= 0)
 
 
+def test_pagerank_residuals_are_l1_changes():
+    """residuals[t] = sum_u |x_{t+1}(u) - x_t(u)|, against the dense Google
+    iteration's own iterates."""
+    A = synth.rmat_csr(7, 900, seed=6)
+    _, res = oracle.pagerank(A.n_rows, A.row_ptr, A.col_idx, 0.85, 12)
+    prev = np.full(A.n_rows, 1.0 / A.n_rows)
+    for t in range(12):
+        cur = google_dense_iterate(A, 0.85, t + 1)
+        np.testing.assert_allclose(res[t], np.abs(cur - prev).sum(), rtol=1e-9, atol=1e-16)
+        prev = cur
+    assert res[0] > 1e-3                       # a skewed graph moves away from 1/N
+
+
 def test_pagerank_uniform_on_regular_graphs():
     for A in (graphs.cycle(19), graphs.complete(11)):
         x, res = oracle.pagerank(A.n_rows, A.row_ptr, A.col_idx, 0.85, 30)

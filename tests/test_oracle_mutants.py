@@ -66,6 +66,19 @@ MUTANTS = {
     "nmf_h_numerator": ("Ht[c * k + r] *= AtW[c * k + r] / (den[r] + eps);",
                         "Ht[c * k + r] *= AtW[c * k + (r + 1) % k] / (den[r] + eps);",
                         [lambda: apps.test_nmf_vs_dense_updates(True)]),
+    # the forward product skips each row's first stored entry
+    "fwd_skips_first_entry": ("for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)\n                    s += vget(",
+                              "for (int64_t p = row_ptr[i] + 1; p < row_ptr[i + 1]; ++p)\n                    s += vget(",
+                              [lambda: sp.test_vs_dense_matmul(0, True, 3), sp.test_ones_give_degrees]),
+    # PageRank's residual adds signed changes (they cancel: both vectors sum to 1)
+    "pr_residual_signed": ("r += fabs(nx[u] - x[u]);", "r += nx[u] - x[u];",
+                           [apps.test_pagerank_residuals_are_l1_changes]),
+    # PageRank spreads the rank of the vertices that have out-links instead of the dangling ones
+    "pr_dangling_inverted": ("if (row_ptr[v + 1] == row_ptr[v]) dangling += x[v];",
+                             "if (row_ptr[v + 1] != row_ptr[v]) dangling += x[v];",
+                             [apps.test_pagerank_two_node_closed_form, apps.test_pagerank_vs_dense_google_matrix]),
+    # NMF objective without ||A||_F^2
+    "nmf_objective_no_a2": ("a2 += a * a;", "a2 += 0.0 * a;", [lambda: apps.test_nmf_vs_dense_updates(True)]),
     # block Lanczos always expands the first block instead of the newest one
     "lanczos_expands_first_block": ("Q + (size_t)(lo + c) * n,", "Q + (size_t)c * n,",
                                     [apps.test_lanczos_vs_dense_eigh_on_rmat, apps.test_lanczos_cycle_closed_form]),

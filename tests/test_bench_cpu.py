@@ -37,3 +37,18 @@ def test_host_cpu_names_the_machine_and_cores():
     import platform
     s = bench.host_cpu()
     assert s.startswith(platform.machine()) and s.endswith(f"{os.cpu_count()} logical cores")
+
+
+def test_algorithmic_bytes_of_the_scale24_sweep():
+    """A once, X once, Y once: nnz * (4 + value bytes) + 8 (N + 1) + N k (x + 4).
+    At R-MAT scale 24 with 2^28 stored entries this is 1.342 GB at k = 1 and
+    9.798 GB at k = 64 (FP32 X, pattern)."""
+    nnz, n = 1 << 28, 1 << 24
+    assert bench.alg_bytes(nnz, n, n, 1, 4) == 4 * nnz + 8 * (n + 1) + 8 * n
+    assert round(bench.alg_bytes(nnz, n, n, 1, 4) / 1e9, 3) == 1.342
+    assert round(bench.alg_bytes(nnz, n, n, 64, 4) / 1e9, 3) == 9.798
+    # a weighted matrix adds its values; BF16 X halves the X side only
+    assert bench.alg_bytes(nnz, n, n, 8, 4, 4) - bench.alg_bytes(nnz, n, n, 8, 4) == 4 * nnz
+    assert bench.alg_bytes(nnz, n, n, 8, 4) - bench.alg_bytes(nnz, n, n, 8, 2) == 2 * 8 * n
+    # one PageRank iteration: the k = 1 A^T product plus the update's five vectors
+    assert bench.pagerank_iter_bytes(nnz, n) == bench.alg_bytes(nnz, n, n, 1, 4) + 20 * n

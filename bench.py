@@ -397,6 +397,36 @@ def base_line(args, metric, value, unit, ms, workload, dtype, extra):
     return line
 
 
+def link_rates_gbs(nbytes=1 << 30, reps=3):
+    """Pinned host <-> device copy rates in GB/s, best of reps: host to
+    device alone, device to host alone, and both at once on two streams
+    (bytes of both directions over the time of the pair).  Host-timed around
+    synchronised copies, so slightly conservative."""
+    import torch
+    hin = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    hout = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    din = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    dout = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(h2d, d2h):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if h2d:
+            with torch.cuda.stream(s_in):
+                din.copy_(hin, non_blocking=True)
+        if d2h:
+            with torch.cuda.stream(s_out):
+                hout.copy_(dout, non_blocking=True)
+        torch.cuda.synchronize()
+        return (int(h2d) + int(d2h)) * nbytes / (time.perf_counter() - t0) / 1e9
+    rates = {"h2d_GBps": max(timed(True, False) for _ in range(reps)),
+             "d2h_GBps": max(timed(False, True) for _ in range(reps)),
+             "both_GBps": max(timed(True, True) for _ in range(reps))}
+    del hin, hout, din, dout
+    return rates
+
+
 def workload_streaming(args):
     """Streaming mode: A (R-MAT, avg degree 32) in pinned host memory, X and Y
     (k = 4, FP32) in HBM; link bytes per call vs the measured pinned H2D peak."""
@@ -1272,6 +1302,15 @@ def main():
                "median_step_ms": round(1e3 * statistics.median(step_s), 2),
                "results_match_device": bool(ok)}
         del Xp, Yp
+        # the link's floor for the step's bytes: both directions at once, or
+        # the slower one-way leg, whichever takes longer
+        try:
+            lr = link_rates_gbs()
+            floor_ms = 1e3 * max((hb + db) / (lr["both_GBps"] * 1e9), hb / (lr["h2d_GBps"] * 1e9),
+                                 db / (lr["d2h_GBps"] * 1e9))
+            e2e["link"] = dict(lr, floor_ms=floor_ms, frac_of_floor=floor_ms / e2e["ms_per_step"])
+        except Exception as ex:                # a report, not a reason to lose the line
+            e2e["link"] = {"error": f"{type(ex).__name__}: {ex}"}
 
     # ---- the same sweep and PageRank on a handle made with SPMM_RELABEL
     # (vertices by decreasing degree): the products with the vectors kept in

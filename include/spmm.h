@@ -554,7 +554,9 @@ int spmm_plan_walk_eff(int64_t n_rows, const int64_t* row_ptr, const spmm_opts* 
  * spmm_plan_runs -- host-only: the runs of whole tasks into which the
  * host-buffer calls (spmm_apply_host, spmm_apply_host_parts) cut a product
  * of the plan spmm_plan_tasks builds, so that a run's rows of Y can be copied
- * out while the next run multiplies (they use 4 runs).  Run j ends at the
+ * out while the next run multiplies (they use 4 runs).  Section 3.4 overlaps
+ * the I/O of one batch of tile rows with the multiplication of another; here
+ * the overlapped I/O is the output's copy to host memory.  Run j ends at the
  * first task that starts at or after (j + 1) / max_runs of the stored entries
  * and begins a new row, so the segments of a split row stay in one run.
  *   row_ptr   n_rows+1 int64 (host)

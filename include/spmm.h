@@ -284,6 +284,9 @@ int spmm_create_tiles(spmm_mat_t* out, int64_t n_rows, int64_t n_cols, int32_t t
  * (the GPU form of keeping many small multiplications busy at once); X and Y
  * are the graphs' dense matrices stacked in graph order (row offsets = the
  * running sums of n_cols for X and n_rows for Y, or the reverse for A^T X).
+ * The paper has no counterpart: it multiplies one graph at a time, with one
+ * task queue over its tile rows (Section 3.4); here one queue covers the
+ * tasks of many graphs.
  *   n_graphs     number of graphs (>= 1)
  *   n_rows[g], n_cols[g]   shape of graph g
  *   row_ptrs[g], col_idxs[g]   host CSR of graph g (local column indices)
@@ -326,7 +329,9 @@ int spmm_apply(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype x
  * computation that keeps its vectors in that order (convert them once with
  * spmm_relabel_rows) pays nothing for the relabelling.  Arguments, errors and
  * asynchrony as spmm_apply; allocates nothing.  On a handle made without
- * SPMM_RELABEL it is spmm_apply.
+ * SPMM_RELABEL it is spmm_apply.  Section 5.1 shows that the vertex order
+ * decides how well the dense rows' reads hit the cache; this is the product
+ * of Section 3 on the reordered graph.
  */
 int spmm_apply_relabelled(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, spmm_dtype xtype, void* Y,
                           int64_t ldy, spmm_dtype ytype, int32_t transpose, void* stream);
@@ -340,8 +345,9 @@ int spmm_apply_relabelled(spmm_mat_t A, const void* X, int64_t ldx, int32_t k, s
  * src, dst  device, row-major, leading dimensions ld_src, ld_dst >= k, element
  *           type dtype (F32, BF16, F16 or F64); they must not overlap
  * Without SPMM_RELABEL it copies.  Asynchronous on `stream`; allocates
- * nothing.  Errors: SPMM_ERR_ARG (NULL, non-square handle, k < 1, ld < k,
- * dtype, src == dst), SPMM_ERR_CUDA.
+ * nothing.  The permutation of a dense matrix's rows that goes with the
+ * vertex reordering of Section 5.1.  Errors: SPMM_ERR_ARG (NULL, non-square
+ * handle, k < 1, ld < k, dtype, src == dst), SPMM_ERR_CUDA.
  */
 int spmm_relabel_rows(spmm_mat_t A, const void* src, int64_t ld_src, int32_t k, spmm_dtype dtype, void* dst,
                       int64_t ld_dst, int32_t to_handle_order, void* stream);
@@ -349,8 +355,8 @@ int spmm_relabel_rows(spmm_mat_t A, const void* src, int64_t ld_src, int32_t k, 
 /*
  * spmm_get_relabel -- the handle's vertex order: old_of_new[v'] (host int32,
  * n entries) is the input vertex that is vertex v' of the handle; the
- * identity without SPMM_RELABEL.  Synchronous.  Errors: SPMM_ERR_ARG (NULL),
- * SPMM_ERR_CUDA.
+ * identity without SPMM_RELABEL (the vertex order of Section 5.1).
+ * Synchronous.  Errors: SPMM_ERR_ARG (NULL), SPMM_ERR_CUDA.
  */
 int spmm_get_relabel(spmm_mat_t A, int32_t* old_of_new);
 
@@ -358,9 +364,11 @@ int spmm_get_relabel(spmm_mat_t A, int32_t* old_of_new);
  * spmm_relabel_order -- host-only: the order SPMM_RELABEL gives an n x n CSR
  * matrix.  Vertex v has degree (row_ptr[v+1] - row_ptr[v]) + (entries with
  * column v); old_of_new lists the vertices by decreasing degree, equal degrees
- * in increasing vertex order.  No GPU is used.  Errors: SPMM_ERR_ARG (n out of
- * range, NULL), SPMM_ERR_FORMAT (row_ptr[0] != 0, decreasing row_ptr, column
- * out of range), SPMM_ERR_OOM.
+ * in increasing vertex order.  No GPU is used.  Section 5.1 compares vertex
+ * orders; this is the degree order, which gathers the hubs of a power-law
+ * graph at the front.  Errors: SPMM_ERR_ARG (n out of range, NULL),
+ * SPMM_ERR_FORMAT (row_ptr[0] != 0, decreasing row_ptr, column out of range),
+ * SPMM_ERR_OOM.
  */
 int spmm_relabel_order(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int32_t* old_of_new);
 
@@ -400,8 +408,9 @@ int spmm_apply_batched(int32_t n, const spmm_mat_t* A, const void* const* X, voi
  * since the last check hit a device-side timeout.  The kernels stage the
  * matrix with asynchronous copies and wait for them with a bound (2 s); a
  * wait that runs out marks the handle, leaves that call's output incomplete
- * and returns SPMM_ERR_TIMEOUT here (the mark is then cleared).  Not a
- * paper operation: the failure-detection side of the asynchronous staging.
+ * and returns SPMM_ERR_TIMEOUT here (the mark is then cleared).  The paper
+ * has no counterpart: this is the failure-detection side of the asynchronous
+ * staging.
  */
 int spmm_sync_status(spmm_mat_t A, void* stream);
 
@@ -512,13 +521,16 @@ int spmm_apply_host_parts(spmm_mat_t A, const void* const* X_parts, float* const
  * wait can never complete (it announces a transfer it never issues), with a
  * bound of wait_ns nanoseconds, and report SPMM_ERR_TIMEOUT when the bound
  * ran out as intended (SPMM_OK would mean the timeout path is broken).
- * Synchronises `stream`; faults nothing.
+ * Synchronises `stream`; faults nothing.  The paper has no counterpart: it
+ * checks the bound that every asynchronous copy's wait carries here.
  */
 int spmm_debug_wait_timeout(uint64_t wait_ns, void* stream);
 
 /*
  * spmm_plan_tasks -- host-only: build the warp-task plan spmm_create_csr
- * would build for this row-pointer array (no GPU work, no device memory).
+ * would build for this row-pointer array (no GPU work, no device memory):
+ * the GPU form of Section 3.4's batches of tile rows, with Section 3.2's
+ * special handling of rows by their number of entries.
  *   row_ptr   n_rows+1 int64 (host)
  *   opts      tuning knobs or NULL
  *   tasks     NULL, or room for *n_tasks + 1 descriptors of 4 int32 each:
@@ -774,6 +786,8 @@ int spmm_replan(spmm_mat_t A, const spmm_opts* opts, int32_t transpose, void* st
  *   best_index    out: index of the fastest candidate
  *   times_ms      host double[number of candidates] or NULL: mean ms each
  * Synchronises `stream`; allocates its workspace.  Errors as spmm_replan.
+ * The paper fixes its tile size and batch sizes by measurement (Sections 3.4,
+ * 5.4); this measures the plan's knobs per matrix and call shape instead.
  */
 int spmm_autotune(spmm_mat_t A, int32_t k, spmm_dtype xtype, int32_t transpose, const spmm_opts* candidates,
                   int32_t n_candidates, int32_t reps, int32_t* best_index, double* times_ms, void* stream);
@@ -795,15 +809,18 @@ int spmm_svds(spmm_mat_t A, int32_t nsv, int32_t block, int32_t max_basis, int32
               spmm_dtype xtype, const double* V0, double* svals, double* right_vecs, double* resid,
               int32_t* restarts_out, void* stream);
 
-/* spmm_get_info -- plan statistics of a handle (host call, no GPU work). */
+/* spmm_get_info -- plan statistics of a handle (host call, no GPU work).
+ * Bookkeeping of this library; the paper has no counterpart. */
 int spmm_get_info(spmm_mat_t A, spmm_info* info);
 
 /* spmm_destroy -- free a handle and its device memory (synchronises the
- * device work that uses it).  NULL is accepted and ignored. */
+ * device work that uses it).  NULL is accepted and ignored.  Bookkeeping of
+ * this library; the paper has no counterpart. */
 int spmm_destroy(spmm_mat_t A);
 
 /* spmm_last_error -- message of the last failing call on this thread
- * ("" if none).  The pointer stays valid until the thread's next call. */
+ * ("" if none).  The pointer stays valid until the thread's next call.
+ * Bookkeeping of this library; the paper has no counterpart. */
 const char* spmm_last_error(void);
 
 #ifdef __cplusplus

@@ -36,6 +36,20 @@ def test_header_declares_the_boundary():
         assert must in names
 
 
+def test_every_entry_point_cites_its_passage():
+    """The comment before each declaration (the nearest one above it) names
+    the paper's passage the call serves (a Section or Algorithm), or says
+    that the paper has no counterpart."""
+    src = open(os.path.join(ROOT, "include", "spmm.h")).read()
+    comments = [(m.end(), m.group(1)) for m in re.finditer(r"/\*(.*?)\*/", src, flags=re.S)]
+    uncited = []
+    for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\**\s*(spmm_\w+)\s*\(", src, flags=re.M):
+        doc = " ".join([c for end, c in comments if end <= m.start()][-1].replace("*", " ").split())
+        if not re.search(r"Section|Algorithm|paper has no counterpart", doc):
+            uncited.append(m.group(1))
+    assert len(comments) > 20 and not uncited, uncited
+
+
 def test_library_exports_every_declared_symbol(lib):
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing

@@ -11,6 +11,7 @@
  *   oracle_spmm        Y = A X and Y = A^T X                (Section 3, Algorithm 1:
  *                      each nonzero a_ij adds a_ij * X[j,:] to output row i)
  *   oracle_spmm_rows   the same for a list of output rows
+ *   oracle_spmm_t_rows A^T X for a list of output rows (columns of A)
  *   oracle_pagerank    PR(u) = (1-d)/N + d * sum_{v in B(u)} PR(v)/L(v)
  *                      (Section 4.1), dangling mass spread uniformly
  *   oracle_nmf         H <- H o (W^T A) / (W^T W H),  W <- W o (A H^T) / (W H H^T)
@@ -20,6 +21,8 @@
  *                      with full re-orthogonalisation; the projection is
  *                      diagonalised by oracle_sym_eigh: Householder
  *                      tridiagonalisation, Sturm bisection, inverse iteration)
+ *   oracle_sym_eigh    all eigenpairs of a small dense symmetric matrix (the
+ *                      Rayleigh-Ritz step of Section 4.2's eigensolver)
  * Types: vtype 0 = pattern (every stored entry is 1), 1 = float32, 2 = float64.
  *        xtype 1 = float32, 2 = float64.  Inputs are read in their own type and
  *        widened to double exactly.
